@@ -1,0 +1,378 @@
+#!/usr/bin/env python
+"""Benchmark of the CE (P, Pdot) search on GB300: folded point-trials per second.
+
+Workload (default): 1000 light curves x 1000 observations (nightly cadence,
+3-year baseline, detached eclipsing binaries), 1e5 log-spaced trial periods,
+Pdot = 0, 15 phase x 10 magnitude bins, per-curve top-5.  One step is one full
+search of that batch through the C ABI (input checks, trial constants,
+per-curve preparation, the persistent CE kernel, the top-k merge), with inputs
+resident on the device; `e2e` repeats it through gce_ce_topk_host with host
+buffers, copies included.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gce|reference]
+Under torchrun each rank searches its own copy of the batch (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import shutil
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "folded point-trials/s (N_obs×N_P×N_Ṗ) on 1 GB300; FP64 vs split-FP32 phase"
+UNIT = "point-trials/s"
+# IMAD-class (integer multiply) instructions per point-trial of each fold's hot
+# loop without Pdot: 3 limb products + 1 bin multiply-high (FIXED32);
+# FP32 pipe ops for SPLIT32; FP64 pipe ops for FP64 (mul, floor, sub, mul, cvt).
+OPS_PER_PT = {"fixed32": 4, "split32": 9, "fp64": 5}
+SM_COUNT = 152
+LANES_PER_SM = {"fixed32": 64, "split32": 128, "fp64": None}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gce", choices=["gce", "reference"])
+    ap.add_argument("--mode", default="fixed32", choices=["fixed32", "split32", "fp64"])
+    ap.add_argument("--workload", type=int, default=1, help="synthetic workload index (0..4)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the FP64 / SPLIT32 / one-launch-per-curve comparison legs")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0,
+                    help="target CPU seconds of the oracle baseline sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+# ---------------------------------------------------------------- oracle leg
+
+def oracle_rate(batch, seconds, n_threads=0):
+    """The CPU oracle on a bounded sample of the workload: the first curves x a
+    strided subset of the periods, sized to take about `seconds`.  Returns
+    (point-trials/s, threads, sample description)."""
+    import oracle
+    orc = oracle.Oracle()
+    n_obs = int(batch.n_obs[0])
+    # calibration run: one curve x 200 periods
+    cal = batch.subset([0], periods=batch.periods[:: max(1, batch.periods.size // 200)])
+    t0 = time.perf_counter()
+    orc.ce_grid(cal.times, cal.mags, cal.offsets, cal.periods, cal.pdots, batch.n_phase,
+                batch.n_mag, n_threads=1)
+    dt = max(time.perf_counter() - t0, 1e-4)
+    rate1 = cal.point_trials / dt
+    threads = os.cpu_count() or 1
+    want = rate1 * threads * seconds
+    n_curves = int(min(batch.n_curves, max(threads, 1)))
+    n_periods = int(min(batch.periods.size, max(64, want / (n_curves * n_obs * batch.pdots.size))))
+    stride = max(1, batch.periods.size // n_periods)
+    sample = batch.subset(list(range(n_curves)), periods=batch.periods[::stride])
+    t0 = time.perf_counter()
+    orc.ce_grid(sample.times, sample.mags, sample.offsets, sample.periods, sample.pdots,
+                batch.n_phase, batch.n_mag, n_threads=n_threads)
+    dt = time.perf_counter() - t0
+    used = orc.threads_used
+    desc = (f"{sample.n_curves} curves x {sample.periods.size} periods (every {stride}th) x "
+            f"{sample.pdots.size} Pdot = {sample.point_trials:.3g} point-trials in {dt:.1f} s")
+    return sample.point_trials / dt, used, desc
+
+
+def run_reference(args, rank, world):
+    """The oracle as the reference arm: timed on the host cores, rank 0 only."""
+    if rank != 0:
+        return
+    import synth
+    batch = synth.make_config(args.workload)
+    per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    rates = []
+    used = 1
+    desc = ""
+    for s in range(args.warmup + args.steps):
+        r, used, desc = oracle_rate(batch, per_step)
+        if s >= args.warmup:
+            rates.append(r)
+    value = float(np.median(rates))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{synth.CONFIG_NAMES[args.workload]}: {batch.n_curves} curves, "
+                               f"{batch.periods.size} periods x {batch.pdots.size} Pdot, "
+                               f"{batch.n_phase}x{batch.n_mag} bins",
+                   "cpu": cpu_model()},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.tmp = None
+
+    def start(self):
+        if not shutil.which("nvidia-smi"):
+            return
+        self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.proc = subprocess.Popen(
+            ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+             "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.tmp,
+            stderr=subprocess.DEVNULL)
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.tmp.flush()
+        self.tmp.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.tmp.read().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.tmp.name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- GPU leg
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+
+    import paper_2006_06866_gb300 as g
+    import synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+
+    batch = synth.make_config(args.workload)
+    k = batch.topk or 5
+    pt_step = batch.point_trials
+    t_d = torch.tensor(batch.times, device=dev)
+    m_d = torch.tensor(batch.mags, device=dev)
+    p_d = torch.tensor(batch.periods, device=dev)
+    q_d = torch.tensor(batch.pdots, device=dev)
+    offs = np.asarray(batch.offsets, dtype=np.int64)
+    h = g.Handle(local)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device=dev)  # 256 MB > L2
+    out_H = torch.empty((batch.n_curves, k), dtype=torch.float32, device=dev)
+    out_I = torch.empty((batch.n_curves, k), dtype=torch.int64, device=dev)
+
+    def step(mode, time_kernel=False):
+        cfg = g.Config(batch.n_phase, batch.n_mag, mode, t0=batch.t0, time_kernel=time_kernel)
+        g.gce_ce_topk(h, t_d, m_d, offs, p_d, q_d, cfg, k, out_H, out_I, stream=stream)
+
+    def timed_steps(mode, warmup, steps, with_kernel=False):
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                step(mode)
+            stream.synchronize()
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(steps)]
+            kern = []
+            barrier()
+            torch.cuda.synchronize()
+            wall0 = time.perf_counter()
+            for i in range(steps):
+                flush.zero_()
+                evs[i][0].record(stream)
+                step(mode, time_kernel=with_kernel)
+                evs[i][1].record(stream)
+                if with_kernel:
+                    kern.append(g.gce_kernel_time(h))
+            stream.synchronize()
+            barrier()
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - wall0
+        st = g.gce_stream_status(h, stream)
+        if st != g.GCE_OK:
+            raise RuntimeError(f"device input check failed: status {st}")
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        return ms, wall, kern
+
+    # ---- headline: the batched persistent kernel in the headline fold mode
+    sampler = ClockSampler(local)
+    sampler.start()
+    ms, wall, kern = timed_steps(args.mode, args.warmup, args.steps, with_kernel=True)
+    clocks = sampler.stop()
+    t_rank = ms / 1e3
+    if pg is not None:
+        tt = torch.tensor([t_rank], device=dev, dtype=torch.float64)
+        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+        t_rank = float(tt.item())
+    value = pt_step * args.steps * world / t_rank
+    ms_per_step = t_rank * 1e3 / args.steps
+    kern_ms = float(np.mean(kern)) if kern else None
+
+    # ---- end to end through the host-buffer entry point (pinned host memory)
+    pin = lambda a: torch.tensor(a).pin_memory()
+    ht, hm, hp, hq = pin(batch.times), pin(batch.mags), pin(batch.periods), pin(batch.pdots)
+    hH = torch.empty((batch.n_curves, k), dtype=torch.float32).pin_memory()
+    hI = torch.empty((batch.n_curves, k), dtype=torch.int64).pin_memory()
+    cfg = g.Config(batch.n_phase, batch.n_mag, args.mode, t0=batch.t0)
+    with torch.cuda.stream(stream):
+        for _ in range(max(1, args.warmup)):
+            g.gce_ce_topk_host(h, ht, hm, offs, hp, hq, cfg, k, hH, hI, stream=stream)
+        barrier()
+        e2e_t = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            stream.synchronize()
+            t0 = time.perf_counter()
+            g.gce_ce_topk_host(h, ht, hm, offs, hp, hq, cfg, k, hH, hI, stream=stream)
+            e2e_t += time.perf_counter() - t0
+    if pg is not None:
+        tt = torch.tensor([e2e_t], device=dev, dtype=torch.float64)
+        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+        e2e_t = float(tt.item())
+    h2d = 8 * (batch.times.size + batch.mags.size + batch.periods.size + batch.pdots.size)
+    d2h = (4 + 8) * batch.n_curves * k
+
+    extras = {}
+    if rank == 0 and world == 1 and not args.no_extras:
+        for mode, n in (("split32", 2), ("fp64", 1)):
+            if mode == args.mode:
+                continue
+            ms_m, _, kern_m = timed_steps(mode, 1, n, with_kernel=True)
+            extras[mode] = {"value": pt_step * n / (ms_m / 1e3), "ms_per_step": ms_m / n,
+                            "kernel_ms": float(np.mean(kern_m))}
+        # the plain FP64 one-launch-per-curve kernel (speedup denominator)
+        cfg64 = g.Config(batch.n_phase, batch.n_mag, "fp64", t0=batch.t0, time_kernel=True)
+        with torch.cuda.stream(stream):
+            out = torch.empty((batch.n_curves, batch.pdots.size, batch.periods.size),
+                              dtype=torch.float32, device=dev)
+            g.gce_ce_grid_single(h, t_d, m_d, offs, p_d, q_d, cfg64, out=out, stream=stream)
+            stream.synchronize()
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g.gce_ce_grid_single(h, t_d, m_d, offs, p_d, q_d, cfg64, out=out, stream=stream)
+            e1.record(stream)
+            stream.synchronize()
+            del out
+        ms_single = e0.elapsed_time(e1)
+        extras["fp64_single_launch"] = {"value": pt_step / (ms_single / 1e3),
+                                        "ms_per_step": ms_single}
+        extras["speedup_vs_fp64_single_launch"] = value / world / extras["fp64_single_launch"]["value"]
+
+    cpu = None
+    if rank == 0 and world == 1:
+        try:
+            r, used, desc = oracle_rate(batch, args.cpu_seconds)
+            cpu = {"value": r, "unit": UNIT, "cores": used, "kind": "oracle", "sample": desc,
+                   "cpu": cpu_model()}
+        except Exception as e:  # the baseline is context; never fail the bench on it
+            cpu = {"value": None, "unit": UNIT, "cores": 0, "kind": "oracle",
+                   "sample": f"unavailable: {e}"}
+
+    roof = None
+    if kern_ms:
+        ops = OPS_PER_PT[args.mode] * pt_step
+        achieved = ops / (kern_ms / 1e3) / 1e9
+        lanes = LANES_PER_SM[args.mode]
+        peak = SM_COUNT * lanes * 2070e6 / 1e9 if lanes else None
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s",
+                "frac": achieved / peak if peak else None, "traffic": None,
+                "kernel": "k_main", "kernel_ms": kern_ms,
+                "kernel_point_trials_per_s": pt_step / (kern_ms / 1e3),
+                "peak_basis": f"{SM_COUNT} SMs x {lanes} integer-multiply lanes/clk x 2070 MHz",
+                "ops_per_point_trial": OPS_PER_PT[args.mode]}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fixed32": "u32", "split32": "f32", "fp64": "f64"}[args.mode],
+            "data": "synthetic",
+            "config": {"workload": f"{synth.CONFIG_NAMES[args.workload]}: {batch.n_curves} curves "
+                                   f"x {int(batch.n_obs.mean())} obs, {batch.periods.size} periods "
+                                   f"x {batch.pdots.size} Pdot, {batch.n_phase}x{batch.n_mag} "
+                                   f"bins, top-{k}",
+                       "phase_mode": args.mode, "point_trials_per_step": pt_step,
+                       "l2": "256 MB buffer written between timed steps",
+                       "parallelism": f"replica per GPU x{world}"},
+            "e2e": {"value": pt_step * args.steps * world / e2e_t, "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": 6 * args.steps,
+            "clocks": clocks,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "modes": extras,
+            "wall_s": wall,
+        }
+        print(json.dumps(line), flush=True)
+    h.close()
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

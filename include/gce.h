@@ -1,0 +1,205 @@
+/*
+ * gce.h -- C ABI of the GB300 conditional-entropy (P, Pdot) search library.
+ *
+ * The library computes, for every light curve of a ragged batch and every trial
+ * (P, Pdot) of a grid, the conditional entropy of Katz et al. (arXiv:2006.06866):
+ *
+ *   fold (Eq. 3, Sec. 2.3):   phi = frac(tau/P - 1/2 Pdot tau^2 / P^2),  tau = t - t0
+ *   bin  (Sec. 2.3):          magnitude bin i from the curve's min..max range,
+ *                             phase bin j = floor(phi * n_phase)
+ *   entropy (Eq. 4):          H = sum_ij p(m_i, phi_j) ln( p(phi_j) / p(m_i, phi_j) )
+ *   selection (Sec. 2.3, 4):  the grid minimum, or the k smallest cells per curve
+ *
+ * Conventions shared by every call:
+ *   - Array arguments are DEVICE pointers (cudaMalloc'd or managed) unless their
+ *     name starts with h_, which marks HOST memory.  The caller owns every input
+ *     and output buffer; the library never frees or keeps them past the call's
+ *     stream work.
+ *   - A ragged batch is (times, mags, h_offsets, n_curves): curve c owns elements
+ *     [h_offsets[c], h_offsets[c+1]) of times and mags (float64); h_offsets is a
+ *     HOST int64 array of n_curves + 1 entries starting at 0, non-decreasing.
+ *   - The trial grid is periods[n_periods] (float64, > 0) x pdots[n_pdots]
+ *     (float64, s/s, any sign -- Sec. 4 notes positive Pdot needs no other
+ *     code).  The flat trial index is q * n_periods + p for pdots[q], periods[p].
+ *   - Units only need to be consistent (e.g. seconds for times and periods).
+ *   - Calls taking a stream are asynchronous on that stream (a cudaStream_t
+ *     passed as void*; NULL is the legacy default stream).  Argument checks that
+ *     need only host data run synchronously and return GCE_ERR_INVALID without
+ *     launching anything.  Checks on device data (non-finite times or
+ *     magnitudes, non-positive or non-finite periods, non-finite pdots, a trial
+ *     range the chosen fold cannot represent) run on the GPU; they are reported
+ *     by gce_stream_status(), and outputs of a flagged call are unspecified.
+ *   - Nothing throws across the ABI.  A handle is not thread-safe: use one per
+ *     host thread.  CUDA failures return GCE_ERR_CUDA with the text available
+ *     from gce_last_error().
+ */
+#ifndef GCE_H
+#define GCE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GCE_OK = 0,
+    GCE_ERR_INVALID = 1,     /* bad argument (host check) or bad input values (device check) */
+    GCE_ERR_CUDA = 2,        /* a CUDA call failed; see gce_last_error() */
+    GCE_ERR_NOMEM = 3,       /* device workspace allocation failed */
+    GCE_ERR_UNSUPPORTED = 4  /* valid input outside what the chosen fold supports */
+} gce_status;
+
+/* How the fold of Eq. 3 is evaluated.  Magnitude bins, counts and the entropy
+ * are the same in every mode; only the phase-bin decision differs. */
+typedef enum {
+    /* binary64 with the operation sequence s = tau*f, b = a*tau,
+     * x = fma(-b, tau, s), phi = x - floor(x), j = floor(phi*n_phase) (clamped),
+     * f = 1/P, a = (0.5*Pdot)*f*f.  Counts are bit-identical to a CPU binary64
+     * evaluation of that sequence. */
+    GCE_PHASE_FP64 = 0,
+    /* FP32 double-float: tau, tau^2, f and a split into (hi, lo) float pairs,
+     * error-free products via fmaf, integer cycles removed with rintf.  Phase
+     * error about 1e-7 cycles; needs |tau|/P < 2^22 cycles. */
+    GCE_PHASE_SPLIT32 = 1,
+    /* fixed point: tau, tau^2, f and a as 64-bit integers split into 32-bit
+     * limbs; the phase is the low 32 bits of their products (integer cycles wrap
+     * away), so the fold is integer multiply-high work.  Phase error a few
+     * 2^-32 cycles; needs |tau|/P < 2^28 and |Pdot| tau^2/P^2 < 2^28 cycles. */
+    GCE_PHASE_FIXED32 = 2
+} gce_phase_mode;
+
+#define GCE_MAX_PHASE_BINS 256
+#define GCE_MAX_MAG_BINS 255
+#define GCE_MAX_CURVE_POINTS 65535
+#define GCE_MAX_TOPK 64
+
+/* flags */
+#define GCE_FLAG_NO_GRAPH 1u      /* launch kernels directly instead of through a CUDA graph */
+#define GCE_FLAG_TIME_KERNEL 2u   /* record CUDA events around the CE kernel (gce_kernel_time) */
+
+typedef struct {
+    int32_t n_phase_bins;  /* 1 .. GCE_MAX_PHASE_BINS (the paper uses 15 and 50) */
+    int32_t n_mag_bins;    /* 1 .. GCE_MAX_MAG_BINS (the paper uses 10) */
+    int32_t phase_mode;    /* gce_phase_mode */
+    uint32_t flags;        /* GCE_FLAG_* */
+    double t0;             /* epoch of the fold, in the unit of times */
+} gce_config;
+
+/* Launch shape of the batched kernel.  block: threads per CTA (64, 128, 256
+ * or 512); tpt: trials per thread (1 or 2); ctas_per_sm: resident CTAs per SM
+ * (0 = as many as fit); chunk: light-curve points staged in shared memory at
+ * once (a multiple of 256, 256 .. 8192). */
+typedef struct {
+    int32_t block;
+    int32_t tpt;
+    int32_t ctas_per_sm;
+    int32_t chunk;
+} gce_tuning;
+
+typedef struct gce_handle_s *gce_handle;
+
+/* Create a handle on CUDA device `device` (it becomes current on the calling
+ * thread).  The handle owns the device workspace, the autotune cache and the
+ * captured CUDA graphs.  *h is NULL on failure. */
+gce_status gce_create(gce_handle *h, int32_t device);
+
+/* Free everything the handle owns (waits for its outstanding work). */
+gce_status gce_destroy(gce_handle h);
+
+/* Static description of a status code; never NULL. */
+const char *gce_status_string(gce_status s);
+
+/* Text of the last failure on this handle ("" if none); valid until the next
+ * call on the handle.  gce_last_error(NULL) describes the last gce_create(). */
+const char *gce_last_error(gce_handle h);
+
+/* Host-side argument checks of a job, without a device or handle.  Returns
+ * GCE_ERR_INVALID if: n_curves < 0; h_offsets NULL (when n_curves > 0), not
+ * starting at 0, decreasing, or any curve empty or longer than
+ * GCE_MAX_CURVE_POINTS; n_periods < 1 or n_pdots < 1 or n_periods * n_pdots >=
+ * 2^32; bins outside their ranges; an unknown phase_mode; k < 0, k >
+ * GCE_MAX_TOPK or k > n_periods * n_pdots. */
+gce_status gce_check_job(const int64_t *h_offsets, int32_t n_curves, int32_t n_periods,
+                         int32_t n_pdots, const gce_config *cfg, int32_t k);
+
+/* Full CE grid (Sec. 2.3, Eq. 3-4): out[(c * n_pdots + q) * n_periods + p] =
+ * H of curve c at (periods[p], pdots[q]) as float32 nats, for every cell.
+ * out must hold n_curves * n_pdots * n_periods floats.  n_curves == 0 is a
+ * no-op. */
+gce_status gce_ce_grid(gce_handle h, const double *times, const double *mags,
+                       const int64_t *h_offsets, int32_t n_curves, const double *periods,
+                       int32_t n_periods, const double *pdots, int32_t n_pdots,
+                       const gce_config *cfg, float *out, void *stream);
+
+/* Per-curve k smallest cells of the CE grid without materialising it (the
+ * selection of Sec. 2.3; batched minima merged as in Sec. 4).  topk_H[c*k + r]
+ * (float32, ascending) and topk_idx[c*k + r] (flat trial index q*n_periods + p)
+ * are the r-th smallest cell; ties in H go to the smaller flat index. */
+gce_status gce_ce_topk(gce_handle h, const double *times, const double *mags,
+                       const int64_t *h_offsets, int32_t n_curves, const double *periods,
+                       int32_t n_periods, const double *pdots, int32_t n_pdots,
+                       const gce_config *cfg, int32_t k, float *topk_H, int64_t *topk_idx,
+                       void *stream);
+
+/* gce_ce_topk on HOST arrays (h_times, h_mags: sum N float64; h_periods,
+ * h_pdots; outputs h_topk_H / h_topk_idx of n_curves * k).  Copies inputs to
+ * the handle's device workspace, runs, copies the results back and waits; the
+ * device-side input checks are folded into the returned status.  Pinned host
+ * memory makes the copies asynchronous DMA; pageable memory works too. */
+gce_status gce_ce_topk_host(gce_handle h, const double *h_times, const double *h_mags,
+                            const int64_t *h_offsets, int32_t n_curves,
+                            const double *h_periods, int32_t n_periods,
+                            const double *h_pdots, int32_t n_pdots, const gce_config *cfg,
+                            int32_t k, float *h_topk_H, int64_t *h_topk_idx, void *stream);
+
+/* Plain baseline: the FP64 fold with one kernel launch per light curve and one
+ * thread per trial (the shape of the paper's own kernel, Sec. 2.3.2), same
+ * output as gce_ce_grid.  cfg->phase_mode must be GCE_PHASE_FP64. */
+gce_status gce_ce_grid_single(gce_handle h, const double *times, const double *mags,
+                              const int64_t *h_offsets, int32_t n_curves,
+                              const double *periods, int32_t n_periods, const double *pdots,
+                              int32_t n_pdots, const gce_config *cfg, float *out,
+                              void *stream);
+
+/* Diagnostic: the full 2-D histogram of selected cells, computed with the same
+ * fold and binning device code as the batched kernel for cfg->phase_mode.
+ * cell_curve / cell_trial: device int64[n_cells] (curve index, flat trial
+ * index).  counts: device uint32[n_cells][n_mag_bins][n_phase_bins]. */
+gce_status gce_ce_counts(gce_handle h, const double *times, const double *mags,
+                         const int64_t *h_offsets, int32_t n_curves, const double *periods,
+                         int32_t n_periods, const double *pdots, int32_t n_pdots,
+                         const gce_config *cfg, int64_t n_cells, const int64_t *cell_curve,
+                         const int64_t *cell_trial, uint32_t *counts, void *stream);
+
+/* Wait for `stream` and report the device-side input checks of the last call
+ * made on this handle (GCE_OK, GCE_ERR_INVALID or GCE_ERR_UNSUPPORTED), or
+ * GCE_ERR_CUDA if the stream failed. */
+gce_status gce_stream_status(gce_handle h, void *stream);
+
+/* Duration in milliseconds of the CE kernel (the persistent fold/histogram/
+ * entropy kernel, without preparation or top-k merge) of the last call made
+ * with GCE_FLAG_TIME_KERNEL, from CUDA events recorded on the call's stream
+ * around that launch.  Waits for the events. */
+gce_status gce_kernel_time(gce_handle h, float *ms);
+
+/* Time candidate launch shapes on a synthetic job of the given size and keep
+ * the fastest for (phase mode, bins, curve-length bucket) in the handle's
+ * cache; later calls with a matching key use it.  Synchronous. */
+gce_status gce_autotune(gce_handle h, const gce_config *cfg, int32_t n_obs_hint,
+                        int64_t n_trials_hint);
+
+/* Read the launch shape the handle would use for a job with this config and
+ * typical curve length, or force one (it then replaces the cached choice for
+ * that key).  gce_set_tuning returns GCE_ERR_INVALID for shapes outside the
+ * documented ranges. */
+gce_status gce_get_tuning(gce_handle h, const gce_config *cfg, int32_t n_obs_hint,
+                          gce_tuning *t);
+gce_status gce_set_tuning(gce_handle h, const gce_config *cfg, int32_t n_obs_hint,
+                          const gce_tuning *t);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GCE_H */

@@ -1,0 +1,737 @@
+// C ABI of the CE search library: argument checks, the handle's device
+// workspace, the per-call kernel sequence (init -> scan -> trial constants ->
+// per-curve prep -> persistent CE kernel -> top-k merge), its capture into
+// CUDA graphs, and the launch-shape autotuner.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <numeric>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "gce_internal.cuh"
+
+using namespace gce;
+
+namespace {
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+typedef std::tuple<int, int, int, int> TuneKey;  // mode, n_phase, n_mag, log2 bucket of N
+
+enum JobKind { JOB_GRID = 0, JOB_TOPK = 1, JOB_SINGLE = 2, JOB_COUNTS = 3 };
+
+struct GraphKey {
+    int kind, mode, n_curves, n_periods, n_pdots, n_phase, n_mag, k, block, tpt, grid, chunk,
+        table_smem, grab;
+    long long n_points;
+    bool operator<(const GraphKey &o) const {
+        return std::tie(kind, mode, n_curves, n_periods, n_pdots, n_phase, n_mag, k, block, tpt,
+                        grid, chunk, table_smem, grab, n_points) <
+               std::tie(o.kind, o.mode, o.n_curves, o.n_periods, o.n_pdots, o.n_phase, o.n_mag,
+                        o.k, o.block, o.tpt, o.grid, o.chunk, o.table_smem, o.grab, o.n_points);
+    }
+};
+
+}  // namespace
+
+struct gce_handle_s {
+    int device = 0;
+    int n_sm = 0;
+    int smem_optin = 0;
+    std::string last_error;
+    DevBuf payload, seg, trialc, order, offsets, cand, table, state, in_times, in_mags,
+        in_periods, in_pdots, out_H, out_idx;
+    int table_n = -1;                    // largest count the table covers
+    int *h_order = nullptr;              // pinned staging
+    long long *h_offsets = nullptr;
+    size_t h_cap = 0;
+    JobState *h_state = nullptr;         // pinned copy target for the check flags
+    cudaEvent_t staged = nullptr;        // staging buffers free again after this
+    bool staged_pending = false;
+    cudaEvent_t k0 = nullptr, k1 = nullptr;  // around the CE kernel (GCE_FLAG_TIME_KERNEL)
+    bool timed = false;
+    std::map<TuneKey, gce_tuning> tune;
+    std::map<GraphKey, cudaGraphExec_t> graphs;
+};
+
+static std::string g_create_error;
+
+static gce_status fail(gce_handle h, gce_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (h) h->last_error = buf;
+    else g_create_error = buf;
+    return st;
+}
+
+#define CUDA_TRY(h, expr)                                                                   \
+    do {                                                                                    \
+        cudaError_t e_ = (expr);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return fail((h), GCE_ERR_CUDA, "%s failed: %s", #expr, cudaGetErrorString(e_)); \
+    } while (0)
+
+static gce_status ensure(gce_handle h, DevBuf &b, size_t bytes) {
+    if (bytes <= b.bytes && b.p) return GCE_OK;
+    size_t want = std::max(bytes, (size_t)256);
+    want = std::max(want, b.bytes + b.bytes / 2);
+    if (b.p) {
+        // in-flight work may still read the old buffer
+        CUDA_TRY(h, cudaDeviceSynchronize());
+        CUDA_TRY(h, cudaFree(b.p));
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    if (cudaMalloc(&b.p, want) != cudaSuccess) {
+        cudaGetLastError();
+        b.p = nullptr;
+        if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            b.p = nullptr;
+            return fail(h, GCE_ERR_NOMEM, "device allocation of %zu bytes failed", bytes);
+        }
+        want = bytes;
+    }
+    b.bytes = want;
+    return GCE_OK;
+}
+
+static int point_bytes(int mode) { return mode == GCE_PHASE_FP64 ? 8 : 16; }
+
+static int ilog2_ceil(long long v) {
+    int e = 0;
+    while ((1ll << e) < v) ++e;
+    return e;
+}
+
+static gce_tuning default_tuning(int mode, int n_max) {
+    gce_tuning t;
+    t.block = 256;
+    t.tpt = 2;
+    t.ctas_per_sm = 0;
+    t.chunk = mode == GCE_PHASE_FP64 ? 4096 : 2048;
+    (void)n_max;
+    return t;
+}
+
+static bool tuning_ok(const gce_tuning &t) {
+    const bool block_ok = t.block == 64 || t.block == 128 || t.block == 256 || t.block == 512;
+    return block_ok && (t.tpt == 1 || t.tpt == 2) && t.ctas_per_sm >= 0 && t.ctas_per_sm <= 32 &&
+           t.chunk >= 256 && t.chunk <= 8192 && t.chunk % 256 == 0;
+}
+
+static TuneKey tune_key(const gce_config *cfg, int n_obs) {
+    return TuneKey(cfg->phase_mode, cfg->n_phase_bins, cfg->n_mag_bins,
+                   ilog2_ceil(std::max(n_obs, 1)));
+}
+
+static gce_tuning lookup_tuning(gce_handle h, const gce_config *cfg, int n_max) {
+    auto it = h->tune.find(tune_key(cfg, n_max));
+    if (it != h->tune.end()) return it->second;
+    return default_tuning(cfg->phase_mode, n_max);
+}
+
+extern "C" const char *gce_status_string(gce_status s) {
+    switch (s) {
+        case GCE_OK: return "ok";
+        case GCE_ERR_INVALID: return "invalid argument or input value";
+        case GCE_ERR_CUDA: return "CUDA error";
+        case GCE_ERR_NOMEM: return "device memory exhausted";
+        case GCE_ERR_UNSUPPORTED: return "input outside the range of the chosen phase fold";
+        default: return "unknown status";
+    }
+}
+
+extern "C" const char *gce_last_error(gce_handle h) {
+    return h ? h->last_error.c_str() : g_create_error.c_str();
+}
+
+extern "C" gce_status gce_check_job(const int64_t *h_offsets, int32_t n_curves,
+                                    int32_t n_periods, int32_t n_pdots, const gce_config *cfg,
+                                    int32_t k) {
+    if (!cfg) return GCE_ERR_INVALID;
+    if (cfg->n_phase_bins < 1 || cfg->n_phase_bins > GCE_MAX_PHASE_BINS) return GCE_ERR_INVALID;
+    if (cfg->n_mag_bins < 1 || cfg->n_mag_bins > GCE_MAX_MAG_BINS) return GCE_ERR_INVALID;
+    if (cfg->phase_mode != GCE_PHASE_FP64 && cfg->phase_mode != GCE_PHASE_SPLIT32 &&
+        cfg->phase_mode != GCE_PHASE_FIXED32)
+        return GCE_ERR_INVALID;
+    if (!std::isfinite(cfg->t0)) return GCE_ERR_INVALID;
+    if (n_curves < 0 || n_periods < 1 || n_pdots < 1) return GCE_ERR_INVALID;
+    const long long n_trials = (long long)n_periods * n_pdots;
+    if (n_trials >= (1ll << 32)) return GCE_ERR_INVALID;
+    if (k < 0 || k > GCE_MAX_TOPK || k > n_trials) return GCE_ERR_INVALID;
+    if (n_curves > 0) {
+        if (!h_offsets || h_offsets[0] != 0) return GCE_ERR_INVALID;
+        for (int32_t c = 0; c < n_curves; ++c) {
+            const long long n = h_offsets[c + 1] - h_offsets[c];
+            if (n < 1 || n > GCE_MAX_CURVE_POINTS) return GCE_ERR_INVALID;
+        }
+    }
+    return GCE_OK;
+}
+
+extern "C" gce_status gce_create(gce_handle *out, int32_t device) {
+    if (!out) return fail(nullptr, GCE_ERR_INVALID, "gce_create: NULL output pointer");
+    *out = nullptr;
+    int n_dev = 0;
+    cudaError_t e = cudaGetDeviceCount(&n_dev);
+    if (e != cudaSuccess)
+        return fail(nullptr, GCE_ERR_CUDA, "cudaGetDeviceCount: %s", cudaGetErrorString(e));
+    if (device < 0 || device >= n_dev)
+        return fail(nullptr, GCE_ERR_INVALID, "device %d out of range (%d devices)", device, n_dev);
+    e = cudaSetDevice(device);
+    if (e != cudaSuccess)
+        return fail(nullptr, GCE_ERR_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    gce_handle h = new (std::nothrow) gce_handle_s();
+    if (!h) return fail(nullptr, GCE_ERR_NOMEM, "host allocation failed");
+    h->device = device;
+    cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, device);
+    cudaDeviceGetAttribute(&h->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    if (cudaEventCreateWithFlags(&h->staged, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreate(&h->k0) != cudaSuccess || cudaEventCreate(&h->k1) != cudaSuccess ||
+        cudaMallocHost((void **)&h->h_state, sizeof(JobState)) != cudaSuccess) {
+        e = cudaGetLastError();
+        gce_destroy(h);
+        return fail(nullptr, GCE_ERR_CUDA, "handle setup: %s", cudaGetErrorString(e));
+    }
+    if (ensure(h, h->state, sizeof(JobState)) != GCE_OK) {
+        gce_destroy(h);
+        return fail(nullptr, GCE_ERR_NOMEM, "workspace allocation failed");
+    }
+    *out = h;
+    return GCE_OK;
+}
+
+extern "C" gce_status gce_destroy(gce_handle h) {
+    if (!h) return GCE_ERR_INVALID;
+    cudaSetDevice(h->device);
+    cudaDeviceSynchronize();
+    for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
+    DevBuf *bufs[] = {&h->payload, &h->seg, &h->trialc, &h->order, &h->offsets, &h->cand,
+                      &h->table, &h->state, &h->in_times, &h->in_mags, &h->in_periods,
+                      &h->in_pdots, &h->out_H, &h->out_idx};
+    for (DevBuf *b : bufs)
+        if (b->p) cudaFree(b->p);
+    if (h->h_order) cudaFreeHost(h->h_order);
+    if (h->h_offsets) cudaFreeHost(h->h_offsets);
+    if (h->h_state) cudaFreeHost(h->h_state);
+    if (h->staged) cudaEventDestroy(h->staged);
+    if (h->k0) cudaEventDestroy(h->k0);
+    if (h->k1) cudaEventDestroy(h->k1);
+    delete h;
+    return GCE_OK;
+}
+
+namespace {
+
+struct Job {
+    int kind;
+    const double *times, *mags, *periods, *pdots;
+    const int64_t *h_offsets;
+    int n_curves, n_periods, n_pdots;
+    const gce_config *cfg;
+    int k;
+    float *out;                  // grid (JOB_GRID, JOB_SINGLE)
+    float *topk_H;               // JOB_TOPK
+    int64_t *topk_idx;
+    long long n_cells;           // JOB_COUNTS
+    const int64_t *cell_curve, *cell_trial;
+    uint32_t *counts;
+    const gce_tuning *force;     // tuning override (autotuner)
+};
+
+struct Plan {
+    long long n_points, n_trials, n_items;
+    int n_max, n_tiles, block, tpt, grid, chunk, table_smem, grab;
+    size_t smem;
+};
+
+gce_status make_plan(gce_handle h, const Job &j, Plan &pl) {
+    const gce_config *cfg = j.cfg;
+    pl.n_points = (long long)j.h_offsets[j.n_curves];
+    pl.n_trials = (long long)j.n_periods * j.n_pdots;
+    long long nmax = 1;
+    for (int c = 0; c < j.n_curves; ++c) nmax = std::max<long long>(nmax, j.h_offsets[c + 1] - j.h_offsets[c]);
+    pl.n_max = (int)nmax;
+    const gce_tuning t = j.force ? *j.force : lookup_tuning(h, cfg, pl.n_max);
+    pl.block = t.block;
+    pl.tpt = t.tpt;
+    pl.chunk = std::min(t.chunk, ((pl.n_max + 31) / 32) * 32);
+    pl.table_smem = std::min(pl.n_max + 1, 2048);
+    const int kk = j.kind == JOB_TOPK ? j.k : 0;
+    pl.smem = main_smem_bytes(cfg->phase_mode, pl.block, pl.tpt, pl.chunk, cfg->n_phase_bins,
+                              cfg->n_mag_bins, pl.table_smem, kk);
+    // shrink the staged chunk (then the table) until the CTA fits
+    while (pl.smem > (size_t)h->smem_optin && pl.chunk > 256) {
+        pl.chunk = std::max(256, pl.chunk / 2);
+        pl.smem = main_smem_bytes(cfg->phase_mode, pl.block, pl.tpt, pl.chunk, cfg->n_phase_bins,
+                                  cfg->n_mag_bins, pl.table_smem, kk);
+    }
+    while (pl.smem > (size_t)h->smem_optin && pl.table_smem > 64) {
+        pl.table_smem /= 2;
+        pl.smem = main_smem_bytes(cfg->phase_mode, pl.block, pl.tpt, pl.chunk, cfg->n_phase_bins,
+                                  cfg->n_mag_bins, pl.table_smem, kk);
+    }
+    if (pl.smem > (size_t)h->smem_optin)
+        return fail(h, GCE_ERR_UNSUPPORTED, "launch shape needs %zu bytes of shared memory", pl.smem);
+    const long long tile = (long long)pl.block * pl.tpt;
+    pl.n_tiles = (int)((pl.n_trials + tile - 1) / tile);
+    pl.n_items = (long long)j.n_curves * pl.n_tiles;
+    CUDA_TRY(h, main_kernel_attrs(cfg->phase_mode, pl.tpt, pl.smem));
+    int occ = 0;
+    CUDA_TRY(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                    &occ, main_kernel_ptr(cfg->phase_mode, pl.tpt), pl.block, pl.smem));
+    if (occ < 1) return fail(h, GCE_ERR_UNSUPPORTED, "launch shape does not fit on an SM");
+    if (t.ctas_per_sm > 0) occ = std::min(occ, t.ctas_per_sm);
+    long long g = (long long)h->n_sm * occ;
+    g = std::min(g, std::max(pl.n_items, 1ll));
+    pl.grid = (int)g;
+    long long grab = pl.n_items / (g * 32);
+    pl.grab = (int)std::max(1ll, std::min(grab, 64ll));
+    return GCE_OK;
+}
+
+// Event around the CE kernel; under stream capture it becomes an event-record node.
+gce_status mark(gce_handle h, cudaEvent_t e, cudaStream_t s, bool capturing) {
+    if (capturing) CUDA_TRY(h, cudaEventRecordWithFlags(e, s, cudaEventRecordExternal));
+    else CUDA_TRY(h, cudaEventRecord(e, s));
+    return GCE_OK;
+}
+
+// Enqueue the whole sequence of one call on stream s (possibly under capture).
+gce_status enqueue(gce_handle h, const Job &j, const Plan &pl, cudaStream_t s, bool capturing) {
+    const gce_config *cfg = j.cfg;
+    const int mode = cfg->phase_mode;
+    JobState *st = (JobState *)h->state.p;
+    CUDA_TRY(h, cudaMemcpyAsync(h->offsets.p, h->h_offsets, sizeof(long long) * (j.n_curves + 1),
+                                cudaMemcpyHostToDevice, s));
+    CUDA_TRY(h, cudaMemcpyAsync(h->order.p, h->h_order, sizeof(int) * j.n_curves,
+                                cudaMemcpyHostToDevice, s));
+    CUDA_TRY(h, launch_init(st, s));
+    CUDA_TRY(h, launch_scan(j.times, j.mags, pl.n_points, j.periods, j.n_periods, j.pdots,
+                            j.n_pdots, cfg->t0, st, s));
+    TrialArgs ta;
+    ta.periods = j.periods;
+    ta.pdots = j.pdots;
+    ta.n_periods = j.n_periods;
+    ta.n_pdots = j.n_pdots;
+    ta.trialc = h->trialc.p;
+    ta.state = st;
+    CUDA_TRY(h, launch_trials(mode, ta, s));
+    PrepArgs pa;
+    pa.times = j.times;
+    pa.mags = j.mags;
+    pa.offsets = (const long long *)h->offsets.p;
+    pa.n_curves = j.n_curves;
+    pa.n_mag = cfg->n_mag_bins;
+    pa.t0 = cfg->t0;
+    pa.payload = h->payload.p;
+    pa.seg = (int *)h->seg.p;
+    pa.state = st;
+    CUDA_TRY(h, launch_prep(mode, pa, s));
+    MainArgs ma;
+    ma.payload = h->payload.p;
+    ma.offsets = (const long long *)h->offsets.p;
+    ma.seg = (const int *)h->seg.p;
+    ma.trialc = h->trialc.p;
+    ma.order = (const int *)h->order.p;
+    ma.table = (const unsigned long long *)h->table.p;
+    ma.n_trials = pl.n_trials;
+    ma.n_tiles = pl.n_tiles;
+    ma.n_items = pl.n_items;
+    ma.grab = pl.grab;
+    ma.n_phase = cfg->n_phase_bins;
+    ma.n_mag = cfg->n_mag_bins;
+    ma.chunk = pl.chunk;
+    ma.table_smem = pl.table_smem;
+    ma.out = nullptr;
+    ma.cand = nullptr;
+    ma.k = 0;
+    ma.state = st;
+    const bool timed = (cfg->flags & GCE_FLAG_TIME_KERNEL) != 0;
+    gce_status ms;
+    switch (j.kind) {
+        case JOB_GRID:
+            ma.out = j.out;
+            if (timed && (ms = mark(h, h->k0, s, capturing)) != GCE_OK) return ms;
+            CUDA_TRY(h, launch_main(mode, pl.tpt, pl.block, pl.grid, pl.smem, ma, s));
+            if (timed && (ms = mark(h, h->k1, s, capturing)) != GCE_OK) return ms;
+            break;
+        case JOB_TOPK:
+            ma.cand = (unsigned long long *)h->cand.p;
+            ma.k = j.k;
+            if (timed && (ms = mark(h, h->k0, s, capturing)) != GCE_OK) return ms;
+            CUDA_TRY(h, launch_main(mode, pl.tpt, pl.block, pl.grid, pl.smem, ma, s));
+            if (timed && (ms = mark(h, h->k1, s, capturing)) != GCE_OK) return ms;
+            CUDA_TRY(h, launch_topk_merge((const unsigned long long *)h->cand.p, j.n_curves,
+                                          pl.n_tiles, j.k, j.topk_H, (long long *)j.topk_idx, st, s));
+            break;
+        case JOB_SINGLE:
+            ma.out = j.out;
+            if (timed && (ms = mark(h, h->k0, s, capturing)) != GCE_OK) return ms;
+            for (int c = 0; c < j.n_curves; ++c) CUDA_TRY(h, launch_single(ma, c, 0, s));
+            if (timed && (ms = mark(h, h->k1, s, capturing)) != GCE_OK) return ms;
+            break;
+        case JOB_COUNTS:
+            CUDA_TRY(h, cudaMemsetAsync(j.counts, 0,
+                                        sizeof(uint32_t) * (size_t)j.n_cells * cfg->n_mag_bins *
+                                            cfg->n_phase_bins, s));
+            CUDA_TRY(h, launch_counts(mode, ma, j.n_cells, (const long long *)j.cell_curve,
+                                      (const long long *)j.cell_trial, (unsigned int *)j.counts, s));
+            break;
+    }
+    return GCE_OK;
+}
+
+gce_status run_job(gce_handle h, const Job &j, cudaStream_t s) {
+    if (!h) return GCE_ERR_INVALID;
+    const gce_status chk = gce_check_job(j.h_offsets, j.n_curves, j.n_periods, j.n_pdots, j.cfg,
+                                         j.kind == JOB_TOPK ? j.k : 0);
+    if (chk != GCE_OK) return fail(h, chk, "argument check failed");
+    if (j.kind == JOB_TOPK && j.k < 1) return fail(h, GCE_ERR_INVALID, "k must be >= 1");
+    if (j.kind == JOB_SINGLE && j.cfg->phase_mode != GCE_PHASE_FP64)
+        return fail(h, GCE_ERR_INVALID, "the one-launch-per-curve baseline is FP64 only");
+    if (j.n_curves == 0) return GCE_OK;
+    if (!j.times || !j.mags || !j.periods || !j.pdots)
+        return fail(h, GCE_ERR_INVALID, "NULL input array");
+    if ((j.kind == JOB_GRID || j.kind == JOB_SINGLE) && !j.out)
+        return fail(h, GCE_ERR_INVALID, "NULL output array");
+    if (j.kind == JOB_TOPK && (!j.topk_H || !j.topk_idx))
+        return fail(h, GCE_ERR_INVALID, "NULL output array");
+    if (j.kind == JOB_COUNTS && j.n_cells > 0 && (!j.cell_curve || !j.cell_trial || !j.counts))
+        return fail(h, GCE_ERR_INVALID, "NULL cell array");
+    CUDA_TRY(h, cudaSetDevice(h->device));
+
+    Plan pl;
+    gce_status st = make_plan(h, j, pl);
+    if (st != GCE_OK) return st;
+    const int mode = j.cfg->phase_mode;
+
+    // workspace
+    if ((st = ensure(h, h->payload, (size_t)point_bytes(mode) * pl.n_points)) != GCE_OK) return st;
+    if ((st = ensure(h, h->seg, sizeof(int) * (size_t)j.n_curves * (j.cfg->n_mag_bins + 1))) != GCE_OK) return st;
+    if ((st = ensure(h, h->trialc, 16 * (size_t)pl.n_trials)) != GCE_OK) return st;
+    if ((st = ensure(h, h->order, sizeof(int) * (size_t)j.n_curves)) != GCE_OK) return st;
+    if ((st = ensure(h, h->offsets, sizeof(long long) * (size_t)(j.n_curves + 1))) != GCE_OK) return st;
+    if (j.kind == JOB_TOPK &&
+        (st = ensure(h, h->cand, 8 * (size_t)j.n_curves * pl.n_tiles * j.k)) != GCE_OK)
+        return st;
+    if (pl.n_max > h->table_n) {
+        if ((st = ensure(h, h->table, 8 * (size_t)(pl.n_max + 1))) != GCE_OK) return st;
+        CUDA_TRY(h, launch_table((unsigned long long *)h->table.p, pl.n_max, s));
+        h->table_n = pl.n_max;
+    }
+
+    // host staging (pinned): offsets and the longest-first curve order
+    if (h->staged_pending) {
+        CUDA_TRY(h, cudaEventSynchronize(h->staged));
+        h->staged_pending = false;
+    }
+    if ((size_t)j.n_curves + 1 > h->h_cap) {
+        if (h->h_order) cudaFreeHost(h->h_order);
+        if (h->h_offsets) cudaFreeHost(h->h_offsets);
+        h->h_order = nullptr;
+        h->h_offsets = nullptr;
+        h->h_cap = 0;
+        size_t cap = (size_t)j.n_curves + 1;
+        CUDA_TRY(h, cudaMallocHost((void **)&h->h_order, sizeof(int) * cap));
+        CUDA_TRY(h, cudaMallocHost((void **)&h->h_offsets, sizeof(long long) * cap));
+        h->h_cap = cap;
+    }
+    std::memcpy(h->h_offsets, j.h_offsets, sizeof(long long) * (j.n_curves + 1));
+    std::iota(h->h_order, h->h_order + j.n_curves, 0);
+    std::stable_sort(h->h_order, h->h_order + j.n_curves, [&](int a, int b) {
+        return j.h_offsets[a + 1] - j.h_offsets[a] > j.h_offsets[b + 1] - j.h_offsets[b];
+    });
+
+    const bool use_graph = !(j.cfg->flags & GCE_FLAG_NO_GRAPH) && s != nullptr &&
+                           j.kind != JOB_SINGLE;
+    h->timed = (j.cfg->flags & GCE_FLAG_TIME_KERNEL) != 0 && j.kind != JOB_COUNTS;
+    if (!use_graph) {
+        st = enqueue(h, j, pl, s, false);
+        if (st != GCE_OK) return st;
+    } else {
+        cudaGraph_t graph = nullptr;
+        CUDA_TRY(h, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        st = enqueue(h, j, pl, s, true);
+        cudaError_t e = cudaStreamEndCapture(s, &graph);
+        if (st != GCE_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (e != cudaSuccess) return fail(h, GCE_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+        GraphKey key{j.kind, mode, j.n_curves, j.n_periods, j.n_pdots, j.cfg->n_phase_bins,
+                     j.cfg->n_mag_bins, j.k, pl.block, pl.tpt, pl.grid, pl.chunk, pl.table_smem,
+                     pl.grab, pl.n_points};
+        auto it = h->graphs.find(key);
+        bool ready = false;
+        if (it != h->graphs.end()) {
+            cudaGraphExecUpdateResultInfo info;
+            if (cudaGraphExecUpdate(it->second, graph, &info) == cudaSuccess) {
+                ready = true;
+            } else {
+                cudaGetLastError();
+                cudaGraphExecDestroy(it->second);
+                h->graphs.erase(it);
+            }
+        }
+        if (!ready) {
+            cudaGraphExec_t exec = nullptr;
+            e = cudaGraphInstantiate(&exec, graph, 0);
+            if (e != cudaSuccess) {
+                cudaGraphDestroy(graph);
+                return fail(h, GCE_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+            }
+            if (h->graphs.size() > 64) {
+                for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
+                h->graphs.clear();
+            }
+            h->graphs[key] = exec;
+        }
+        cudaGraphDestroy(graph);
+        CUDA_TRY(h, cudaGraphLaunch(h->graphs[key], s));
+    }
+    CUDA_TRY(h, cudaEventRecord(h->staged, s));
+    h->staged_pending = true;
+    return GCE_OK;
+}
+
+gce_status state_status(gce_handle h) {
+    const unsigned int e = h->h_state->err;
+    if (e & (ERR_TIME | ERR_PERIOD | ERR_PDOT))
+        return fail(h, GCE_ERR_INVALID, "device check: %s%s%s",
+                    (e & ERR_TIME) ? "non-finite time or magnitude; " : "",
+                    (e & ERR_PERIOD) ? "non-finite or non-positive period; " : "",
+                    (e & ERR_PDOT) ? "non-finite period derivative; " : "");
+    if (e & ERR_RANGE)
+        return fail(h, GCE_ERR_UNSUPPORTED, "device check: trial range beyond the phase fold's range");
+    return GCE_OK;
+}
+
+}  // namespace
+
+extern "C" gce_status gce_ce_grid(gce_handle h, const double *times, const double *mags,
+                                  const int64_t *h_offsets, int32_t n_curves,
+                                  const double *periods, int32_t n_periods, const double *pdots,
+                                  int32_t n_pdots, const gce_config *cfg, float *out,
+                                  void *stream) {
+    Job j{};
+    j.kind = JOB_GRID;
+    j.times = times; j.mags = mags; j.h_offsets = h_offsets; j.n_curves = n_curves;
+    j.periods = periods; j.n_periods = n_periods; j.pdots = pdots; j.n_pdots = n_pdots;
+    j.cfg = cfg; j.out = out;
+    return run_job(h, j, (cudaStream_t)stream);
+}
+
+extern "C" gce_status gce_ce_topk(gce_handle h, const double *times, const double *mags,
+                                  const int64_t *h_offsets, int32_t n_curves,
+                                  const double *periods, int32_t n_periods, const double *pdots,
+                                  int32_t n_pdots, const gce_config *cfg, int32_t k,
+                                  float *topk_H, int64_t *topk_idx, void *stream) {
+    Job j{};
+    j.kind = JOB_TOPK;
+    j.times = times; j.mags = mags; j.h_offsets = h_offsets; j.n_curves = n_curves;
+    j.periods = periods; j.n_periods = n_periods; j.pdots = pdots; j.n_pdots = n_pdots;
+    j.cfg = cfg; j.k = k; j.topk_H = topk_H; j.topk_idx = topk_idx;
+    return run_job(h, j, (cudaStream_t)stream);
+}
+
+extern "C" gce_status gce_ce_grid_single(gce_handle h, const double *times, const double *mags,
+                                         const int64_t *h_offsets, int32_t n_curves,
+                                         const double *periods, int32_t n_periods,
+                                         const double *pdots, int32_t n_pdots,
+                                         const gce_config *cfg, float *out, void *stream) {
+    Job j{};
+    j.kind = JOB_SINGLE;
+    j.times = times; j.mags = mags; j.h_offsets = h_offsets; j.n_curves = n_curves;
+    j.periods = periods; j.n_periods = n_periods; j.pdots = pdots; j.n_pdots = n_pdots;
+    j.cfg = cfg; j.out = out;
+    return run_job(h, j, (cudaStream_t)stream);
+}
+
+extern "C" gce_status gce_ce_counts(gce_handle h, const double *times, const double *mags,
+                                    const int64_t *h_offsets, int32_t n_curves,
+                                    const double *periods, int32_t n_periods,
+                                    const double *pdots, int32_t n_pdots, const gce_config *cfg,
+                                    int64_t n_cells, const int64_t *cell_curve,
+                                    const int64_t *cell_trial, uint32_t *counts, void *stream) {
+    if (n_cells < 0) return GCE_ERR_INVALID;
+    Job j{};
+    j.kind = JOB_COUNTS;
+    j.times = times; j.mags = mags; j.h_offsets = h_offsets; j.n_curves = n_curves;
+    j.periods = periods; j.n_periods = n_periods; j.pdots = pdots; j.n_pdots = n_pdots;
+    j.cfg = cfg; j.n_cells = n_cells; j.cell_curve = cell_curve; j.cell_trial = cell_trial;
+    j.counts = counts;
+    return run_job(h, j, (cudaStream_t)stream);
+}
+
+extern "C" gce_status gce_stream_status(gce_handle h, void *stream) {
+    if (!h) return GCE_ERR_INVALID;
+    CUDA_TRY(h, cudaSetDevice(h->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(h, cudaMemcpyAsync(h->h_state, h->state.p, sizeof(JobState), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(h, cudaStreamSynchronize(s));
+    return state_status(h);
+}
+
+extern "C" gce_status gce_ce_topk_host(gce_handle h, const double *h_times, const double *h_mags,
+                                       const int64_t *h_offsets, int32_t n_curves,
+                                       const double *h_periods, int32_t n_periods,
+                                       const double *h_pdots, int32_t n_pdots,
+                                       const gce_config *cfg, int32_t k, float *h_topk_H,
+                                       int64_t *h_topk_idx, void *stream) {
+    if (!h) return GCE_ERR_INVALID;
+    gce_status st = gce_check_job(h_offsets, n_curves, n_periods, n_pdots, cfg, k);
+    if (st != GCE_OK) return fail(h, st, "argument check failed");
+    if (k < 1) return fail(h, GCE_ERR_INVALID, "k must be >= 1");
+    if (n_curves == 0) return GCE_OK;
+    if (!h_times || !h_mags || !h_periods || !h_pdots || !h_topk_H || !h_topk_idx)
+        return fail(h, GCE_ERR_INVALID, "NULL host array");
+    CUDA_TRY(h, cudaSetDevice(h->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t np = (size_t)h_offsets[n_curves];
+    if ((st = ensure(h, h->in_times, 8 * np)) != GCE_OK) return st;
+    if ((st = ensure(h, h->in_mags, 8 * np)) != GCE_OK) return st;
+    if ((st = ensure(h, h->in_periods, 8 * (size_t)n_periods)) != GCE_OK) return st;
+    if ((st = ensure(h, h->in_pdots, 8 * (size_t)n_pdots)) != GCE_OK) return st;
+    if ((st = ensure(h, h->out_H, 4 * (size_t)n_curves * k)) != GCE_OK) return st;
+    if ((st = ensure(h, h->out_idx, 8 * (size_t)n_curves * k)) != GCE_OK) return st;
+    CUDA_TRY(h, cudaMemcpyAsync(h->in_times.p, h_times, 8 * np, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(h, cudaMemcpyAsync(h->in_mags.p, h_mags, 8 * np, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(h, cudaMemcpyAsync(h->in_periods.p, h_periods, 8 * (size_t)n_periods,
+                                cudaMemcpyHostToDevice, s));
+    CUDA_TRY(h, cudaMemcpyAsync(h->in_pdots.p, h_pdots, 8 * (size_t)n_pdots,
+                                cudaMemcpyHostToDevice, s));
+    st = gce_ce_topk(h, (const double *)h->in_times.p, (const double *)h->in_mags.p, h_offsets,
+                     n_curves, (const double *)h->in_periods.p, n_periods,
+                     (const double *)h->in_pdots.p, n_pdots, cfg, k, (float *)h->out_H.p,
+                     (int64_t *)h->out_idx.p, stream);
+    if (st != GCE_OK) return st;
+    CUDA_TRY(h, cudaMemcpyAsync(h_topk_H, h->out_H.p, 4 * (size_t)n_curves * k,
+                                cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(h, cudaMemcpyAsync(h_topk_idx, h->out_idx.p, 8 * (size_t)n_curves * k,
+                                cudaMemcpyDeviceToHost, s));
+    return gce_stream_status(h, stream);
+}
+
+extern "C" gce_status gce_kernel_time(gce_handle h, float *ms) {
+    if (!h || !ms) return GCE_ERR_INVALID;
+    if (!h->timed) return fail(h, GCE_ERR_INVALID, "the last call was not made with GCE_FLAG_TIME_KERNEL");
+    CUDA_TRY(h, cudaEventSynchronize(h->k1));
+    CUDA_TRY(h, cudaEventElapsedTime(ms, h->k0, h->k1));
+    return GCE_OK;
+}
+
+// ------------------------------------------------------------------ tuning
+
+extern "C" gce_status gce_get_tuning(gce_handle h, const gce_config *cfg, int32_t n_obs_hint,
+                                     gce_tuning *t) {
+    if (!h || !cfg || !t) return GCE_ERR_INVALID;
+    *t = lookup_tuning(h, cfg, std::max(1, n_obs_hint));
+    return GCE_OK;
+}
+
+extern "C" gce_status gce_set_tuning(gce_handle h, const gce_config *cfg, int32_t n_obs_hint,
+                                     const gce_tuning *t) {
+    if (!h || !cfg || !t || !tuning_ok(*t)) return GCE_ERR_INVALID;
+    h->tune[tune_key(cfg, std::max(1, n_obs_hint))] = *t;
+    return GCE_OK;
+}
+
+extern "C" gce_status gce_autotune(gce_handle h, const gce_config *cfg, int32_t n_obs_hint,
+                                   int64_t n_trials_hint) {
+    if (!h || !cfg) return GCE_ERR_INVALID;
+    const int n_obs = std::max(16, std::min<int>(n_obs_hint, GCE_MAX_CURVE_POINTS));
+    const long long n_tr = std::max<long long>(4096, std::min<long long>(n_trials_hint, 1 << 22));
+    int64_t offs[9];
+    const int n_curves = 8;
+    for (int c = 0; c <= n_curves; ++c) offs[c] = (int64_t)c * n_obs;
+    if (gce_check_job(offs, n_curves, (int32_t)n_tr, 1, cfg, 0) != GCE_OK)
+        return fail(h, GCE_ERR_INVALID, "autotune: invalid config");
+    CUDA_TRY(h, cudaSetDevice(h->device));
+    // synthetic job: 3-year times, a square-ish signal, log-spaced periods
+    const size_t np = (size_t)n_curves * n_obs;
+    std::vector<double> t(np), m(np), per((size_t)n_tr), pd(1, 0.0);
+    unsigned long long x = 0x9e3779b97f4a7c15ull;
+    auto u01 = [&x]() {
+        x ^= x << 13; x ^= x >> 7; x ^= x << 17;
+        return (double)(x >> 11) * (1.0 / 9007199254740992.0);
+    };
+    for (size_t i = 0; i < np; ++i) {
+        t[i] = u01() * 9.46e7;
+        m[i] = 15.0 + (u01() < 0.1 ? 0.5 : 0.0) + 0.02 * u01();
+    }
+    for (long long p = 0; p < n_tr; ++p) per[p] = 300.0 * std::pow(288.0, (double)p / (double)(n_tr - 1));
+    double *d_t = nullptr, *d_m = nullptr, *d_p = nullptr, *d_d = nullptr;
+    float *d_out = nullptr;
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    gce_status result = GCE_OK;
+    gce_tuning best = default_tuning(cfg->phase_mode, n_obs);
+    float best_ms = 1e30f;
+    const int blocks[] = {128, 256, 512};
+    const int tpts[] = {1, 2};
+    gce_config c2 = *cfg;
+    c2.flags |= GCE_FLAG_NO_GRAPH;
+    do {
+        if (cudaMalloc(&d_t, 8 * np) || cudaMalloc(&d_m, 8 * np) || cudaMalloc(&d_p, 8 * n_tr) ||
+            cudaMalloc(&d_d, 8) || cudaMalloc(&d_out, 4 * np / n_obs * n_tr) ||
+            cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) || cudaEventCreate(&e0) ||
+            cudaEventCreate(&e1)) {
+            result = fail(h, GCE_ERR_NOMEM, "autotune: allocation failed");
+            break;
+        }
+        cudaMemcpy(d_t, t.data(), 8 * np, cudaMemcpyHostToDevice);
+        cudaMemcpy(d_m, m.data(), 8 * np, cudaMemcpyHostToDevice);
+        cudaMemcpy(d_p, per.data(), 8 * n_tr, cudaMemcpyHostToDevice);
+        cudaMemcpy(d_d, pd.data(), 8, cudaMemcpyHostToDevice);
+        for (int b : blocks) {
+            for (int tp : tpts) {
+                gce_tuning cand = default_tuning(cfg->phase_mode, n_obs);
+                cand.block = b;
+                cand.tpt = tp;
+                Job j{};
+                j.kind = JOB_GRID;
+                j.times = d_t; j.mags = d_m; j.h_offsets = offs; j.n_curves = n_curves;
+                j.periods = d_p; j.n_periods = (int)n_tr; j.pdots = d_d; j.n_pdots = 1;
+                j.cfg = &c2; j.out = d_out; j.force = &cand;
+                gce_status st = run_job(h, j, s);
+                if (st != GCE_OK) continue;  // shape does not fit: skip it
+                cudaEventRecord(e0, s);
+                for (int rep = 0; rep < 3; ++rep) run_job(h, j, s);
+                cudaEventRecord(e1, s);
+                if (cudaEventSynchronize(e1) != cudaSuccess) {
+                    result = fail(h, GCE_ERR_CUDA, "autotune: %s", cudaGetErrorString(cudaGetLastError()));
+                    break;
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = cand;
+                }
+            }
+            if (result != GCE_OK) break;
+        }
+    } while (0);
+    if (s) cudaStreamSynchronize(s);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (s) cudaStreamDestroy(s);
+    cudaFree(d_t); cudaFree(d_m); cudaFree(d_p); cudaFree(d_d); cudaFree(d_out);
+    if (result == GCE_OK) h->tune[tune_key(cfg, n_obs)] = best;
+    return result;
+}

@@ -1,0 +1,244 @@
+// Internal definitions shared by the library's translation units: job state,
+// per-point and per-trial payloads of the three fold modes, the folds
+// themselves (Eq. 3 of arXiv:2006.06866) and the fixed-point entropy table
+// (Eq. 4).  Nothing here is part of the C ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/gce.h"
+
+namespace gce {
+
+// ------------------------------------------------------------------ job state
+
+// Device-side state of one call: reductions of the scan kernel, input-check
+// flags and the persistent kernel's work counter.  Zeroed (pmin set to +inf)
+// by k_init at the start of every call.
+struct JobState {
+    unsigned long long tau_max_bits;    // max |t - t0| as binary64 bits
+    unsigned long long pmin_bits;       // min period as binary64 bits
+    unsigned long long pdot_max_bits;   // max |Pdot| as binary64 bits
+    unsigned long long work;            // next work item (persistent kernel)
+    unsigned int err;                   // ERR_* bits
+    unsigned int pad[3];
+};
+
+enum : unsigned int {
+    ERR_TIME = 1u,      // non-finite time or magnitude
+    ERR_PERIOD = 2u,    // non-finite or non-positive period
+    ERR_PDOT = 4u,      // non-finite period derivative
+    ERR_RANGE = 8u,     // trial range beyond what the chosen fold represents
+};
+
+// Fixed-point scaling of the FIXED32 fold, derived from the job's maxima.
+// tau_max < 2^e_tau.  T = tau 2^s (|T| < 2^62), F = f 2^r with s + r = 96, so
+// T F / 2^64 = tau f 2^32; U = tau^2 2^u (U < 2^62), A = a 2^v with
+// u + v = 96, so U A / 2^64 = a tau^2 2^32.
+struct FixedScale {
+    int e_tau;
+    int s, r, u, v;
+};
+
+__host__ __device__ inline FixedScale fixed_scale_from(double tau_max) {
+    FixedScale fs;
+    int e = 0;
+    if (tau_max > 0.0) {
+        int ex;
+        frexp(tau_max, &ex);   // tau_max = m 2^ex, m in [0.5, 1)  =>  tau_max < 2^ex
+        e = ex;
+    }
+    fs.e_tau = e;
+    fs.s = 62 - e;
+    fs.r = 96 - fs.s;
+    fs.u = 62 - 2 * e;
+    fs.v = 96 - fs.u;
+    return fs;
+}
+
+// ------------------------------------------------------------------ payloads
+
+// Per point, sorted by magnitude bin, in the layout of the fold mode.
+//   FP64:    double tau                                        (8 bytes)
+//   SPLIT32: float4 {tau_hi, tau_lo, tau2_hi, tau2_lo}          (16 bytes)
+//   FIXED32: uint4  {T1 (int32), T0, U1, U0 (int32, balanced)}  (16 bytes)
+// Per flat trial:
+//   FP64:    double2 {f, a}
+//   SPLIT32: float4  {f_hi, f_lo, a_hi, a_lo}
+//   FIXED32: uint4   {F1, F0 (int32, balanced), An1 (int32), An0} with An = -A
+template <int MODE> struct ModeTraits;
+template <> struct ModeTraits<GCE_PHASE_FP64> {
+    typedef double point_t;
+    typedef double2 trial_t;
+};
+template <> struct ModeTraits<GCE_PHASE_SPLIT32> {
+    typedef float4 point_t;
+    typedef float4 trial_t;
+};
+template <> struct ModeTraits<GCE_PHASE_FIXED32> {
+    typedef uint4 point_t;
+    typedef uint4 trial_t;
+};
+
+// Balanced split of a 64-bit value: x = hi 2^32 + lo with lo a signed 32-bit
+// value in [-2^31, 2^31), so that signed multiply-high works on it.
+__host__ __device__ inline void split_balanced(long long x, int *hi, int *lo) {
+    long long h = x >> 32;  // arithmetic
+    unsigned int l = (unsigned int)(x & 0xffffffffll);
+    if (l >= 0x80000000u) h += 1;
+    *hi = (int)h;
+    *lo = (int)l;  // two's complement reinterpretation: l - 2^32 when l >= 2^31
+}
+
+// ------------------------------------------------------------------ folds
+
+// Eq. 3 in binary64 with the pinned operation sequence (see gce.h); returns the
+// phase bin.  With pdot == false, a is known to be +-0 and x = s exactly.
+template <bool PDOT>
+__device__ __forceinline__ int fold_fp64(double tau, double f, double a, double nphi,
+                                         int n_phase) {
+    double s = __dmul_rn(tau, f);
+    double x = s;
+    if (PDOT) {
+        double b = __dmul_rn(a, tau);
+        x = __fma_rn(-b, tau, s);
+    }
+    double phi = __dsub_rn(x, floor(x));
+    int j = __double2int_rd(__dmul_rn(phi, nphi));
+    return min(j, n_phase - 1);
+}
+
+// Eq. 3 in FP32 double-float.  tau f = th fh + (th fl + tl fh) (+ tl fl, below
+// 2^-48 relative): p = RN(th fh) with its exact error e = fma(th, fh, -p)
+// (Dekker's product via FMA); the integer cycles of p are removed exactly with
+// rintf; the small cross terms are added to e.  The Pdot term a tau^2 is
+// treated the same way with tau^2 = t2h + t2l and a = ah + al.
+template <bool PDOT>
+__device__ __forceinline__ int fold_split(float4 pt, float4 tr, float nphi, int n_phase) {
+    const float th = pt.x, tl = pt.y;
+    const float fh = tr.x, fl = tr.y;
+    float p = __fmul_rn(th, fh);
+    float e = __fmaf_rn(th, fh, -p);
+    float r = __fsub_rn(p, rintf(p));
+    float c = __fmaf_rn(th, fl, __fmaf_rn(tl, fh, e));
+    if (PDOT) {
+        const float t2h = pt.z, t2l = pt.w;
+        const float ah = tr.z, al = tr.w;
+        float q = __fmul_rn(ah, t2h);
+        float e2 = __fmaf_rn(ah, t2h, -q);
+        float r2 = __fsub_rn(q, rintf(q));
+        float c2 = __fmaf_rn(al, t2h, __fmaf_rn(ah, t2l, e2));
+        r = __fsub_rn(r, r2);
+        c = __fsub_rn(c, c2);
+    }
+    float x = __fadd_rn(r, c);
+    float ph = __fsub_rn(x, floorf(x));
+    int j = __float2int_rz(__fmul_rn(ph, nphi));
+    return min(j, n_phase - 1);
+}
+
+// Eq. 3 in 32-bit-limb fixed point.  With T = T1 2^32 + T0 and F = F1 2^32 + F0
+// (F0 balanced), bits 64..95 of T F -- the phase in units of 2^-32 cycles, the
+// integer cycles having wrapped out of the 32-bit word -- are
+//   lo32(T1 F1) + hi32(T1 F0) + hi32(T0 F1)     (dropped carries: -1..+2 units).
+// The Pdot term is the same product for U (tau^2) and An = -A (a); then the
+// phase bin is floor(phase n_phase / 2^32) = hi32(phase n_phase).
+template <bool PDOT>
+__device__ __forceinline__ int fold_fixed(uint4 pt, uint4 tr, unsigned int n_phase) {
+    const int T1 = (int)pt.x;
+    const unsigned int T0 = pt.y;
+    const unsigned int F1 = tr.x;
+    const int F0 = (int)tr.y;
+    unsigned int acc = (unsigned int)T1 * F1;
+    acc += (unsigned int)__mulhi(T1, F0);
+    acc += __umulhi(T0, F1);
+    if (PDOT) {
+        const unsigned int U1 = pt.z;
+        const int U0 = (int)pt.w;
+        const int A1 = (int)tr.z;
+        const unsigned int A0 = tr.w;
+        acc += U1 * (unsigned int)A1;
+        acc += (unsigned int)__mulhi(A1, U0);
+        acc += __umulhi(A0, U1);
+    }
+    return (int)__umulhi(acc, n_phase);
+}
+
+// ------------------------------------------------------------------ entropy
+
+// Fixed-point table of c ln c: tab[c] = round(c ln(c) 2^32), tab[0] = tab[1] = 0.
+// Eq. 4 rewritten with integer counts is
+//   N H = sum_j c_j ln c_j - sum_ij c_ij ln c_ij,
+// and summing the table's integers makes both sums exact and independent of
+// order; the only error is the table's rounding (at most 2^-33 per term).
+constexpr double kTabScale = 4294967296.0;  // 2^32
+constexpr double kTabInvScale = 1.0 / 4294967296.0;
+
+// ------------------------------------------------------------------ launches
+
+struct PrepArgs {
+    const double *times;
+    const double *mags;
+    const long long *offsets;  // device copy, n_curves + 1
+    int n_curves;
+    int n_mag;
+    double t0;
+    void *payload;             // ModeTraits<MODE>::point_t[sum N], sorted by mag bin per curve
+    int *seg;                  // [n_curves][n_mag + 1] segment starts (relative to the curve)
+    const JobState *state;
+};
+
+struct TrialArgs {
+    const double *periods;
+    const double *pdots;
+    int n_periods;
+    int n_pdots;
+    void *trialc;              // ModeTraits<MODE>::trial_t[n_periods * n_pdots]
+    JobState *state;
+};
+
+struct MainArgs {
+    const void *payload;
+    const long long *offsets;
+    const int *seg;
+    const void *trialc;
+    const int *order;          // curves in processing order (longest first)
+    const unsigned long long *table;
+    long long n_trials;
+    int n_tiles;               // trial tiles per curve
+    long long n_items;         // n_curves * n_tiles
+    int grab;                  // items taken per work-counter increment
+    int n_phase;
+    int n_mag;
+    int chunk;                 // points staged per pass
+    int table_smem;            // table entries staged in shared memory
+    float *out;                // grid or nullptr
+    unsigned long long *cand;  // top-k candidates [n_curves][n_tiles][k] or nullptr
+    int k;
+    JobState *state;
+};
+
+// Kernel launchers (defined in the .cu files).
+cudaError_t launch_init(JobState *st, cudaStream_t s);
+cudaError_t launch_scan(const double *times, const double *mags, long long n_points,
+                        const double *periods, int n_periods, const double *pdots, int n_pdots,
+                        double t0, JobState *st, cudaStream_t s);
+cudaError_t launch_trials(int mode, const TrialArgs &a, cudaStream_t s);
+cudaError_t launch_prep(int mode, const PrepArgs &a, cudaStream_t s);
+cudaError_t launch_table(unsigned long long *table, int n_max, cudaStream_t s);
+size_t main_smem_bytes(int mode, int block, int tpt, int chunk, int n_phase, int n_mag,
+                       int table_smem, int k);
+cudaError_t main_kernel_attrs(int mode, int tpt, size_t smem);
+const void *main_kernel_ptr(int mode, int tpt);
+cudaError_t launch_main(int mode, int tpt, int block, int grid, size_t smem,
+                        const MainArgs &a, cudaStream_t s);
+cudaError_t launch_topk_merge(const unsigned long long *cand, int n_curves, int n_tiles,
+                              int k, float *topk_H, long long *topk_idx, const JobState *st,
+                              cudaStream_t s);
+cudaError_t launch_single(const MainArgs &a, int curve, long long n_points, cudaStream_t s);
+cudaError_t launch_counts(int mode, const MainArgs &a, long long n_cells,
+                          const long long *cell_curve, const long long *cell_trial,
+                          unsigned int *counts, cudaStream_t s);
+
+}  // namespace gce

@@ -1,0 +1,436 @@
+// The CE hot path: fold (Eq. 3) -> phase x magnitude histogram (Sec. 2.3) ->
+// entropy (Eq. 4) -> grid or per-curve top-k (Sec. 2.3, Sec. 4).
+//
+// Work decomposition.  One thread owns TPT trials (P, Pdot) of one light curve
+// -- the paper's thread-per-grid-point design (Sec. 2.3.2) -- and a CTA owns a
+// tile of block * TPT consecutive flat trial indices.  A work item is one
+// (curve, tile) pair; CTAs are persistent and take items from one atomic
+// counter, longest curves first.  The curve's points, regrouped by magnitude
+// bin during preparation, are staged in shared memory and read by every thread
+// as broadcasts.  Because the points arrive one magnitude bin at a time, each
+// thread needs only a 1-D phase histogram per trial (the paper's
+// 1/n_mag-memory observation): counters are cumulative u16 [trial][phase bin]
+// arrays private to the thread, and at the end of each magnitude segment the
+// difference against a snapshot gives that segment's c_ij.
+//
+// Entropy.  N H = sum_j c_j ln c_j - sum_ij c_ij ln c_ij, accumulated as exact
+// 64-bit integers from a fixed-point c ln c table (2^32 scale); H is converted
+// to float32 once per trial.
+#include <cmath>
+#include <cstdint>
+
+#include "gce_internal.cuh"
+
+namespace gce {
+
+namespace {
+
+constexpr unsigned long long kNoKey = ~0ull;
+
+__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w < v ? w : v;
+    }
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long tab_lookup(const unsigned long long *s_tab,
+                                                         int table_smem,
+                                                         const unsigned long long *g_tab,
+                                                         int c) {
+    return c < table_smem ? s_tab[c] : __ldg(g_tab + c);
+}
+
+template <int MODE> struct Fold;
+template <> struct Fold<GCE_PHASE_FP64> {
+    template <bool PDOT>
+    __device__ __forceinline__ static int bin(double p, double2 t, double nphi_d, float,
+                                              int n_phase) {
+        return fold_fp64<PDOT>(p, t.x, t.y, nphi_d, n_phase);
+    }
+    __device__ __forceinline__ static bool has_pdot(double2 t) { return t.y != 0.0; }
+};
+template <> struct Fold<GCE_PHASE_SPLIT32> {
+    template <bool PDOT>
+    __device__ __forceinline__ static int bin(float4 p, float4 t, double, float nphi_f,
+                                              int n_phase) {
+        return fold_split<PDOT>(p, t, nphi_f, n_phase);
+    }
+    __device__ __forceinline__ static bool has_pdot(float4 t) {
+        return t.z != 0.0f || t.w != 0.0f;
+    }
+};
+template <> struct Fold<GCE_PHASE_FIXED32> {
+    template <bool PDOT>
+    __device__ __forceinline__ static int bin(uint4 p, uint4 t, double, float, int n_phase) {
+        return fold_fixed<PDOT>(p, t, (unsigned int)n_phase);
+    }
+    __device__ __forceinline__ static bool has_pdot(uint4 t) { return (t.z | t.w) != 0u; }
+};
+
+// The hot loop: every point of [ka, kb) (shared memory, broadcast) folded for
+// the thread's TPT trials and counted into the thread's private counters.
+template <int MODE, int TPT, bool PDOT>
+__device__ __forceinline__ void count_points(
+    const typename ModeTraits<MODE>::point_t *__restrict__ pts, int ka, int kb,
+    const typename ModeTraits<MODE>::trial_t (&tc)[TPT], unsigned short *cnt, int stride_j,
+    int stride_s, double nphi_d, float nphi_f, int n_phase) {
+#pragma unroll 2
+    for (int k = ka; k < kb; ++k) {
+        const typename ModeTraits<MODE>::point_t p = pts[k];
+#pragma unroll
+        for (int s = 0; s < TPT; ++s) {
+            const int j = Fold<MODE>::template bin<PDOT>(p, tc[s], nphi_d, nphi_f, n_phase);
+            unsigned short *cp = cnt + s * stride_s + j * stride_j;
+            *cp = (unsigned short)(*cp + 1);
+        }
+    }
+}
+
+template <int MODE, int TPT>
+__global__ void __launch_bounds__(512, 1) k_main(MainArgs a) {
+    typedef typename ModeTraits<MODE>::point_t point_t;
+    typedef typename ModeTraits<MODE>::trial_t trial_t;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ long long s_item;
+
+    if (a.state->err) return;  // inputs failed the device checks: no work
+
+    const int B = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int n_phase = a.n_phase, n_mag = a.n_mag;
+    const int stride_j = B, stride_s = n_phase * B;
+
+    point_t *s_pts = reinterpret_cast<point_t *>(smem);
+    unsigned long long *s_tab = reinterpret_cast<unsigned long long *>(s_pts + a.chunk);
+    unsigned short *s_cnt = reinterpret_cast<unsigned short *>(s_tab + a.table_smem);
+    unsigned short *s_prev = s_cnt + TPT * n_phase * B;
+    int *s_seg = reinterpret_cast<int *>(s_prev + TPT * n_phase * B);
+    unsigned long long *s_top =
+        reinterpret_cast<unsigned long long *>(s_seg + ((n_mag + 2) & ~1));
+
+    for (int i = tid; i < a.table_smem; i += B) s_tab[i] = a.table[i];
+
+    const point_t *g_pts = reinterpret_cast<const point_t *>(a.payload);
+    const trial_t *g_tr = reinterpret_cast<const trial_t *>(a.trialc);
+    const double nphi_d = (double)n_phase;
+    const float nphi_f = (float)n_phase;
+    unsigned short *my_cnt = s_cnt + tid;
+    unsigned short *my_prev = s_prev + tid;
+
+    int staged_curve = -1, staged_lo = -1;
+    long long item = 0, item_end = 0;
+    for (;;) {
+        if (item >= item_end) {
+            __syncthreads();
+            if (tid == 0) s_item = (long long)atomicAdd(&a.state->work, (unsigned long long)a.grab);
+            __syncthreads();
+            item = s_item;
+            item_end = min(item + (long long)a.grab, a.n_items);
+            if (item >= a.n_items) break;
+        }
+        const int ci = (int)(item / a.n_tiles);
+        const int tile = (int)(item - (long long)ci * a.n_tiles);
+        const int c = a.order[ci];
+        const long long off = a.offsets[c];
+        const int n = (int)(a.offsets[c + 1] - off);
+        if (c != staged_curve) {
+            __syncthreads();
+            for (int i = tid; i <= n_mag; i += B) s_seg[i] = a.seg[(long long)c * (n_mag + 1) + i];
+            staged_curve = c;
+            staged_lo = -1;
+        }
+
+        trial_t tc[TPT];
+        long long tt[TPT];
+        bool any_pdot = false;
+#pragma unroll
+        for (int s = 0; s < TPT; ++s) {
+            tt[s] = (long long)tile * (B * TPT) + (long long)s * B + tid;
+            if (tt[s] < a.n_trials) {
+                tc[s] = g_tr[tt[s]];
+                any_pdot |= Fold<MODE>::has_pdot(tc[s]);
+            } else {
+                tc[s] = trial_t{};
+            }
+        }
+        const bool pdot = __syncthreads_or(any_pdot) != 0;
+
+        for (int i = 0; i < TPT * n_phase; ++i) {
+            my_cnt[i * B] = 0;
+            my_prev[i * B] = 0;
+        }
+        unsigned long long s_ij[TPT];
+#pragma unroll
+        for (int s = 0; s < TPT; ++s) s_ij[s] = 0ull;
+
+        for (int lo = 0; lo < n; lo += a.chunk) {
+            const int hi = min(n, lo + a.chunk);
+            if (staged_lo != lo) {
+                __syncthreads();
+                const point_t *src = g_pts + off + lo;
+                for (int k = tid; k < hi - lo; k += B) s_pts[k] = src[k];
+                __syncthreads();
+                staged_lo = lo;
+            }
+            for (int i = 0; i < n_mag; ++i) {
+                const int s0 = s_seg[i], s1 = s_seg[i + 1];
+                const int ka = max(s0, lo), kb = min(s1, hi);
+                if (ka < kb) {
+                    if (pdot)
+                        count_points<MODE, TPT, true>(s_pts - lo, ka, kb, tc, my_cnt, stride_j,
+                                                      stride_s, nphi_d, nphi_f, n_phase);
+                    else
+                        count_points<MODE, TPT, false>(s_pts - lo, ka, kb, tc, my_cnt, stride_j,
+                                                       stride_s, nphi_d, nphi_f, n_phase);
+                }
+                if (s1 > s0 && s1 > lo && s1 <= hi) {
+                    // end of magnitude segment i: c_ij = counter - snapshot
+#pragma unroll
+                    for (int s = 0; s < TPT; ++s) {
+                        unsigned long long acc = 0ull;
+                        for (int j = 0; j < n_phase; ++j) {
+                            const int o = s * stride_s + j * stride_j;
+                            const int cur = my_cnt[o];
+                            const int cij = cur - (int)my_prev[o];
+                            my_prev[o] = (unsigned short)cur;
+                            acc += tab_lookup(s_tab, a.table_smem, a.table, cij);
+                        }
+                        s_ij[s] += acc;
+                    }
+                }
+            }
+        }
+
+        // sum_j c_j ln c_j from the cumulative counters, then H
+        const double inv = kTabInvScale / (double)n;
+        unsigned long long key[TPT];
+#pragma unroll
+        for (int s = 0; s < TPT; ++s) {
+            unsigned long long sj = 0ull;
+            for (int j = 0; j < n_phase; ++j)
+                sj += tab_lookup(s_tab, a.table_smem, a.table, my_cnt[s * stride_s + j * stride_j]);
+            long long d = (long long)(sj - s_ij[s]);
+            if (d < 0) d = 0;
+            const float h = __double2float_rn(__dmul_rn(__ll2double_rn(d), inv));
+            key[s] = kNoKey;
+            if (tt[s] < a.n_trials) {
+                if (a.out) a.out[(long long)c * a.n_trials + tt[s]] = h;
+                key[s] = ((unsigned long long)__float_as_uint(h) << 32) | (unsigned long long)tt[s];
+            }
+        }
+
+        if (a.cand) {
+            // tile top-k: k rounds of warp minima, then one warp merges the warps' lists
+            const int nw = B >> 5;
+            for (int r = 0; r < a.k; ++r) {
+                unsigned long long mine = key[0];
+#pragma unroll
+                for (int s = 1; s < TPT; ++s) mine = key[s] < mine ? key[s] : mine;
+                const unsigned long long m = warp_min_u64(mine);
+                if (lane == 0) s_top[warp * a.k + r] = m;
+#pragma unroll
+                for (int s = 0; s < TPT; ++s)
+                    if (key[s] == m) key[s] = kNoKey;
+            }
+            __syncthreads();
+            if (warp == 0) {
+                unsigned long long *dst = a.cand + ((long long)c * a.n_tiles + tile) * a.k;
+                const int tot = nw * a.k;
+                for (int r = 0; r < a.k; ++r) {
+                    unsigned long long mine = kNoKey;
+                    for (int i = lane; i < tot; i += 32) mine = s_top[i] < mine ? s_top[i] : mine;
+                    const unsigned long long m = warp_min_u64(mine);
+                    for (int i = lane; i < tot; i += 32)
+                        if (s_top[i] == m) s_top[i] = kNoKey;
+                    __syncwarp();
+                    if (lane == 0) dst[r] = m;
+                }
+            }
+        }
+        ++item;
+    }
+}
+
+// Per-curve merge of the tiles' candidates: k rounds of "smallest key above the
+// previous one" (keys are unique: H bits in the high word, trial index low).
+__global__ void k_topk_merge(const unsigned long long *__restrict__ cand, int n_tiles, int k,
+                             float *topk_H, long long *topk_idx, const JobState *st) {
+    __shared__ unsigned long long sh[32];
+    if (st->err) return;
+    const int c = blockIdx.x;
+    const long long n = (long long)n_tiles * k;
+    const unsigned long long *src = cand + (long long)c * n;
+    unsigned long long last = 0ull;
+    for (int r = 0; r < k; ++r) {
+        unsigned long long mine = kNoKey;
+        for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+            const unsigned long long v = src[i];
+            if ((r == 0 || v > last) && v < mine) mine = v;
+        }
+        mine = warp_min_u64(mine);
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mine;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            unsigned long long v = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : kNoKey;
+            v = warp_min_u64(v);
+            if (threadIdx.x == 0) sh[0] = v;
+        }
+        __syncthreads();
+        last = sh[0];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            topk_H[(long long)c * k + r] = __uint_as_float((unsigned int)(last >> 32));
+            topk_idx[(long long)c * k + r] = (long long)(last & 0xffffffffull);
+        }
+    }
+}
+
+// The plain baseline: one launch per curve, one thread per trial, the FP64
+// fold, points read straight from global memory.
+__global__ void __launch_bounds__(256) k_single(MainArgs a, int c) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    if (a.state->err) return;
+    const int B = blockDim.x, tid = threadIdx.x;
+    const int n_phase = a.n_phase, n_mag = a.n_mag;
+    unsigned short *cnt = reinterpret_cast<unsigned short *>(smem) + tid;
+    unsigned short *prev = cnt + n_phase * B;
+    const long long t = (long long)blockIdx.x * B + tid;
+    const bool valid = t < a.n_trials;
+    const double2 tr = valid ? reinterpret_cast<const double2 *>(a.trialc)[t] : double2{0.0, 0.0};
+    const double *pts = reinterpret_cast<const double *>(a.payload) + a.offsets[c];
+    const int *seg = a.seg + (long long)c * (n_mag + 1);
+    const int n = (int)(a.offsets[c + 1] - a.offsets[c]);
+    for (int j = 0; j < n_phase; ++j) {
+        cnt[j * B] = 0;
+        prev[j * B] = 0;
+    }
+    unsigned long long s_ij = 0ull;
+    for (int i = 0; i < n_mag; ++i) {
+        const int s0 = seg[i], s1 = seg[i + 1];
+        if (s1 == s0) continue;
+        for (int k = s0; k < s1; ++k) {
+            const int j = fold_fp64<true>(__ldg(pts + k), tr.x, tr.y, (double)n_phase, n_phase);
+            cnt[j * B] = (unsigned short)(cnt[j * B] + 1);
+        }
+        for (int j = 0; j < n_phase; ++j) {
+            const int cur = cnt[j * B];
+            s_ij += __ldg(a.table + (cur - prev[j * B]));
+            prev[j * B] = (unsigned short)cur;
+        }
+    }
+    unsigned long long sj = 0ull;
+    for (int j = 0; j < n_phase; ++j) sj += __ldg(a.table + cnt[j * B]);
+    long long d = (long long)(sj - s_ij);
+    if (d < 0) d = 0;
+    if (valid)
+        a.out[(long long)c * a.n_trials + t] =
+            __double2float_rn(__dmul_rn(__ll2double_rn(d), kTabInvScale / (double)n));
+}
+
+// Diagnostic: full 2-D counts of selected cells through the same fold code.
+template <int MODE>
+__global__ void k_counts(MainArgs a, long long n_cells, const long long *cell_curve,
+                         const long long *cell_trial, unsigned int *counts) {
+    typedef typename ModeTraits<MODE>::point_t point_t;
+    typedef typename ModeTraits<MODE>::trial_t trial_t;
+    if (a.state->err) return;
+    const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= n_cells) return;
+    const long long c = cell_curve[cell], t = cell_trial[cell];
+    const trial_t tr = reinterpret_cast<const trial_t *>(a.trialc)[t];
+    const point_t *pts = reinterpret_cast<const point_t *>(a.payload) + a.offsets[c];
+    const int *seg = a.seg + c * (a.n_mag + 1);
+    unsigned int *out = counts + cell * a.n_mag * a.n_phase;
+    const bool pdot = Fold<MODE>::has_pdot(tr);
+    for (int i = 0; i < a.n_mag; ++i) {
+        for (int k = seg[i]; k < seg[i + 1]; ++k) {
+            const int j = pdot ? Fold<MODE>::template bin<true>(pts[k], tr, (double)a.n_phase,
+                                                                (float)a.n_phase, a.n_phase)
+                               : Fold<MODE>::template bin<false>(pts[k], tr, (double)a.n_phase,
+                                                                 (float)a.n_phase, a.n_phase);
+            out[i * a.n_phase + j] += 1u;
+        }
+    }
+}
+
+template <int MODE, int TPT>
+cudaError_t launch_main_t(int block, int grid, size_t smem, const MainArgs &a, cudaStream_t s) {
+    k_main<MODE, TPT><<<grid, block, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t main_smem_bytes(int mode, int block, int tpt, int chunk, int n_phase, int n_mag,
+                       int table_smem, int k) {
+    size_t pt = mode == GCE_PHASE_FP64 ? 8 : 16;
+    size_t b = pt * (size_t)chunk + 8 * (size_t)table_smem +
+               2 * 2 * (size_t)tpt * n_phase * block + 4 * (size_t)((n_mag + 2) & ~1) +
+               8 * (size_t)(block / 32) * (size_t)(k > 0 ? k : 1);
+    return b;
+}
+
+const void *main_kernel_ptr(int mode, int tpt) {
+    switch (mode * 4 + tpt) {
+        case GCE_PHASE_FP64 * 4 + 1: return (const void *)k_main<GCE_PHASE_FP64, 1>;
+        case GCE_PHASE_FP64 * 4 + 2: return (const void *)k_main<GCE_PHASE_FP64, 2>;
+        case GCE_PHASE_SPLIT32 * 4 + 1: return (const void *)k_main<GCE_PHASE_SPLIT32, 1>;
+        case GCE_PHASE_SPLIT32 * 4 + 2: return (const void *)k_main<GCE_PHASE_SPLIT32, 2>;
+        case GCE_PHASE_FIXED32 * 4 + 1: return (const void *)k_main<GCE_PHASE_FIXED32, 1>;
+        case GCE_PHASE_FIXED32 * 4 + 2: return (const void *)k_main<GCE_PHASE_FIXED32, 2>;
+        default: return nullptr;
+    }
+}
+
+cudaError_t main_kernel_attrs(int mode, int tpt, size_t smem) {
+    const void *f = main_kernel_ptr(mode, tpt);
+    if (!f) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t launch_main(int mode, int tpt, int block, int grid, size_t smem, const MainArgs &a,
+                        cudaStream_t s) {
+    switch (mode * 4 + tpt) {
+        case GCE_PHASE_FP64 * 4 + 1: return launch_main_t<GCE_PHASE_FP64, 1>(block, grid, smem, a, s);
+        case GCE_PHASE_FP64 * 4 + 2: return launch_main_t<GCE_PHASE_FP64, 2>(block, grid, smem, a, s);
+        case GCE_PHASE_SPLIT32 * 4 + 1: return launch_main_t<GCE_PHASE_SPLIT32, 1>(block, grid, smem, a, s);
+        case GCE_PHASE_SPLIT32 * 4 + 2: return launch_main_t<GCE_PHASE_SPLIT32, 2>(block, grid, smem, a, s);
+        case GCE_PHASE_FIXED32 * 4 + 1: return launch_main_t<GCE_PHASE_FIXED32, 1>(block, grid, smem, a, s);
+        case GCE_PHASE_FIXED32 * 4 + 2: return launch_main_t<GCE_PHASE_FIXED32, 2>(block, grid, smem, a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_topk_merge(const unsigned long long *cand, int n_curves, int n_tiles, int k,
+                              float *topk_H, long long *topk_idx, const JobState *st,
+                              cudaStream_t s) {
+    if (n_curves <= 0) return cudaSuccess;
+    k_topk_merge<<<n_curves, 256, 0, s>>>(cand, n_tiles, k, topk_H, topk_idx, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_single(const MainArgs &a, int curve, long long, cudaStream_t s) {
+    const int B = 256;
+    const long long g = (a.n_trials + B - 1) / B;
+    const size_t smem = 2 * 2 * (size_t)a.n_phase * B;
+    k_single<<<(unsigned int)g, B, smem, s>>>(a, curve);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_counts(int mode, const MainArgs &a, long long n_cells,
+                          const long long *cell_curve, const long long *cell_trial,
+                          unsigned int *counts, cudaStream_t s) {
+    if (n_cells <= 0) return cudaSuccess;
+    const int B = 128;
+    const unsigned int g = (unsigned int)((n_cells + B - 1) / B);
+    switch (mode) {
+        case GCE_PHASE_FP64: k_counts<GCE_PHASE_FP64><<<g, B, 0, s>>>(a, n_cells, cell_curve, cell_trial, counts); break;
+        case GCE_PHASE_SPLIT32: k_counts<GCE_PHASE_SPLIT32><<<g, B, 0, s>>>(a, n_cells, cell_curve, cell_trial, counts); break;
+        default: k_counts<GCE_PHASE_FIXED32><<<g, B, 0, s>>>(a, n_cells, cell_curve, cell_trial, counts); break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace gce

@@ -1,0 +1,296 @@
+// Trial-independent preparation (O(sum N + n_trials)): input checks and
+// maxima, per-trial fold constants, per-curve magnitude binning with the
+// points regrouped by magnitude bin, and the c ln c fixed-point table.
+#include <cmath>
+#include <cstdint>
+
+#include "gce_internal.cuh"
+
+namespace gce {
+
+namespace {
+
+constexpr unsigned long long kPosInfBits = 0x7ff0000000000000ull;
+
+__global__ void k_init(JobState *st) {
+    st->tau_max_bits = 0ull;
+    st->pmin_bits = kPosInfBits;
+    st->pdot_max_bits = 0ull;
+    st->err = 0u;
+    st->work = 0ull;
+}
+
+// Non-negative binary64 values order like their bit patterns, so maxima and
+// minima reduce with 64-bit integer atomics.
+__device__ inline void atomic_max_pos(unsigned long long *dst, double v) {
+    atomicMax(dst, (unsigned long long)__double_as_longlong(v));
+}
+__device__ inline void atomic_min_pos(unsigned long long *dst, double v) {
+    atomicMin(dst, (unsigned long long)__double_as_longlong(v));
+}
+
+__device__ inline double warp_max(double v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ inline double warp_min(double v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Checks every time, magnitude, period and period derivative; reduces
+// max |t - t0|, min P and max |Pdot|.
+__global__ void k_scan(const double *__restrict__ times, const double *__restrict__ mags,
+                       long long n_points, const double *__restrict__ periods, int n_periods,
+                       const double *__restrict__ pdots, int n_pdots, double t0, JobState *st) {
+    unsigned int err = 0u;
+    double tmax = 0.0, pmin = INFINITY, dmax = 0.0;
+    long long stride = (long long)gridDim.x * blockDim.x;
+    long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (long long i = i0; i < n_points; i += stride) {
+        double t = times[i], m = mags[i];
+        if (!isfinite(t) || !isfinite(m)) err |= ERR_TIME;
+        double tau = fabs(t - t0);
+        if (isfinite(tau)) tmax = fmax(tmax, tau);
+        else err |= ERR_TIME;
+    }
+    for (long long i = i0; i < n_periods; i += stride) {
+        double p = periods[i];
+        if (!isfinite(p) || !(p > 0.0)) err |= ERR_PERIOD;
+        else pmin = fmin(pmin, p);
+    }
+    for (long long i = i0; i < n_pdots; i += stride) {
+        double d = pdots[i];
+        if (!isfinite(d)) err |= ERR_PDOT;
+        else dmax = fmax(dmax, fabs(d));
+    }
+    tmax = warp_max(tmax);
+    dmax = warp_max(dmax);
+    pmin = warp_min(pmin);
+    err = __reduce_or_sync(0xffffffffu, err);
+    if ((threadIdx.x & 31) == 0) {
+        if (tmax > 0.0) atomic_max_pos(&st->tau_max_bits, tmax);
+        if (dmax > 0.0) atomic_max_pos(&st->pdot_max_bits, dmax);
+        if (pmin < INFINITY) atomic_min_pos(&st->pmin_bits, pmin);
+        if (err) atomicOr(&st->err, err);
+    }
+}
+
+// Per flat trial t = q n_periods + p: f = 1/P, a = (0.5 Pdot) f f (the oracle's
+// sequence), stored in the fold mode's format.
+template <int MODE>
+__global__ void k_trials(TrialArgs a) {
+    typedef typename ModeTraits<MODE>::trial_t trial_t;
+    trial_t *out = reinterpret_cast<trial_t *>(a.trialc);
+    const long long n = (long long)a.n_periods * a.n_pdots;
+    const double tau_max = __longlong_as_double((long long)a.state->tau_max_bits);
+    const FixedScale fs = fixed_scale_from(tau_max);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        // Range of the fold (checked once, from the maxima).
+        const double pmin = __longlong_as_double((long long)a.state->pmin_bits);
+        const double dmax = __longlong_as_double((long long)a.state->pdot_max_bits);
+        if (pmin < INFINITY && pmin > 0.0) {
+            const double fmax_ = 1.0 / pmin;
+            const double amax = 0.5 * dmax * fmax_ * fmax_;
+            bool bad = false;
+            if (MODE == GCE_PHASE_SPLIT32) {
+                bad = tau_max * fmax_ >= 4194304.0 || amax * tau_max * tau_max >= 4194304.0;
+            } else if (MODE == GCE_PHASE_FIXED32) {
+                bad = ldexp(fmax_, fs.e_tau) >= 536870912.0 ||
+                      ldexp(amax, 2 * fs.e_tau) >= 536870912.0;
+            }
+            if (bad) atomicOr(&a.state->err, ERR_RANGE);
+        }
+    }
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int p = (int)(t % a.n_periods);
+        const int q = (int)(t / a.n_periods);
+        const double f = 1.0 / a.periods[p];
+        const double aa = (0.5 * a.pdots[q]) * f * f;
+        trial_t v;
+        if constexpr (MODE == GCE_PHASE_FP64) {
+            v.x = f;
+            v.y = aa;
+        } else if constexpr (MODE == GCE_PHASE_SPLIT32) {
+            float fh = __double2float_rn(f);
+            float ah = __double2float_rn(aa);
+            v.x = fh;
+            v.y = __double2float_rn(f - (double)fh);
+            v.z = ah;
+            v.w = __double2float_rn(aa - (double)ah);
+        } else {
+            // Out-of-range values are flagged above; clamp so the conversions stay defined.
+            double F = fmin(ldexp(f, fs.r), 9.2e18);
+            double A = fmax(fmin(ldexp(aa, fs.v), 9.2e18), -9.2e18);
+            int f1, f0, a1, a0;
+            split_balanced(__double2ll_rn(F), &f1, &f0);
+            long long an = -__double2ll_rn(A);
+            a1 = (int)(an >> 32);
+            a0 = (int)(unsigned int)(an & 0xffffffffll);
+            v.x = (unsigned int)f1;
+            v.y = (unsigned int)f0;
+            v.z = (unsigned int)a1;
+            v.w = (unsigned int)a0;
+        }
+        out[t] = v;
+    }
+}
+
+constexpr int kPrepBlock = 256;
+
+__device__ inline double block_reduce(double v, bool is_max, double *sh) {
+    v = is_max ? warp_max(v) : warp_min(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        v = l < (blockDim.x >> 5) ? sh[l] : (is_max ? -INFINITY : INFINITY);
+        v = is_max ? warp_max(v) : warp_min(v);
+        if (l == 0) sh[0] = v;
+    }
+    __syncthreads();
+    v = sh[0];
+    __syncthreads();
+    return v;
+}
+
+// Magnitude bin of Sec. 2.3 with the oracle's operation sequence:
+// i = floor(((m - mn) / (mx - mn)) * n_mag), clamped; mx == mn -> 0.
+__device__ inline int mag_bin(double m, double mn, double mx, int n_mag) {
+    if (mx == mn) return 0;
+    double v = __ddiv_rn(__dsub_rn(m, mn), __dsub_rn(mx, mn));
+    int i = __double2int_rd(__dmul_rn(v, (double)n_mag));
+    return min(i, n_mag - 1);
+}
+
+// One CTA per curve: min/max of the magnitudes, magnitude bins, a counting sort
+// of the points by magnitude bin (segment starts written to seg), and the
+// points' fold payload written in the sorted order.  The order of points inside
+// a segment is arbitrary; counts do not depend on it.
+template <int MODE>
+__global__ void __launch_bounds__(kPrepBlock) k_prep(PrepArgs a) {
+    typedef typename ModeTraits<MODE>::point_t point_t;
+    __shared__ double sh_red[32];
+    __shared__ int hist[GCE_MAX_MAG_BINS + 1];
+    const int c = blockIdx.x;
+    const long long lo = a.offsets[c];
+    const int n = (int)(a.offsets[c + 1] - lo);
+    const double *m = a.mags + lo;
+    const double *t = a.times + lo;
+    double mn = INFINITY, mx = -INFINITY;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        mn = fmin(mn, m[k]);
+        mx = fmax(mx, m[k]);
+    }
+    mn = block_reduce(mn, false, sh_red);
+    mx = block_reduce(mx, true, sh_red);
+    for (int i = threadIdx.x; i <= a.n_mag; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    for (int k = threadIdx.x; k < n; k += blockDim.x) atomicAdd(&hist[mag_bin(m[k], mn, mx, a.n_mag)], 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        int *seg = a.seg + (long long)c * (a.n_mag + 1);
+        for (int i = 0; i < a.n_mag; ++i) {
+            int h = hist[i];
+            hist[i] = run;
+            seg[i] = run;
+            run += h;
+        }
+        seg[a.n_mag] = run;
+    }
+    __syncthreads();
+    const FixedScale fs = fixed_scale_from(__longlong_as_double((long long)a.state->tau_max_bits));
+    point_t *out = reinterpret_cast<point_t *>(a.payload) + lo;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const int pos = atomicAdd(&hist[mag_bin(m[k], mn, mx, a.n_mag)], 1);
+        const double tau = __dsub_rn(t[k], a.t0);
+        point_t v;
+        if constexpr (MODE == GCE_PHASE_FP64) {
+            v = tau;
+        } else if constexpr (MODE == GCE_PHASE_SPLIT32) {
+            const double tau2 = __dmul_rn(tau, tau);
+            float th = __double2float_rn(tau);
+            float t2h = __double2float_rn(tau2);
+            v.x = th;
+            v.y = __double2float_rn(tau - (double)th);
+            v.z = t2h;
+            v.w = __double2float_rn(tau2 - (double)t2h);
+        } else {
+            // T = round(tau 2^s), |T| < 2^62; U = floor(T^2 / 2^62) = tau^2 2^u
+            // computed exactly from T in 128-bit integer arithmetic.
+            const long long T = __double2ll_rn(ldexp(tau, fs.s));
+            const unsigned long long aT = (unsigned long long)(T < 0 ? -T : T);
+            const unsigned long long hi = __umul64hi(aT, aT), lw = aT * aT;
+            const long long U = (long long)((hi << 2) | (lw >> 62));
+            int u1, u0;
+            split_balanced(U, &u1, &u0);
+            v.x = (unsigned int)(int)(T >> 32);
+            v.y = (unsigned int)(T & 0xffffffffll);
+            v.z = (unsigned int)u1;
+            v.w = (unsigned int)u0;
+        }
+        out[pos] = v;
+    }
+}
+
+__global__ void k_table(unsigned long long *table, int n_max) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c <= n_max; c += gridDim.x * blockDim.x) {
+        double v = c > 1 ? (double)c * log((double)c) * kTabScale : 0.0;
+        table[c] = (unsigned long long)__double2ll_rn(v);
+    }
+}
+
+int grid_for(long long n, int block, int cap) {
+    long long g = (n + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (int)g;
+}
+
+}  // namespace
+
+cudaError_t launch_init(JobState *st, cudaStream_t s) {
+    k_init<<<1, 1, 0, s>>>(st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan(const double *times, const double *mags, long long n_points,
+                        const double *periods, int n_periods, const double *pdots, int n_pdots,
+                        double t0, JobState *st, cudaStream_t s) {
+    long long n = n_points;
+    if (n_periods > n) n = n_periods;
+    if (n_pdots > n) n = n_pdots;
+    k_scan<<<grid_for(n, 256, 1216), 256, 0, s>>>(times, mags, n_points, periods, n_periods,
+                                                     pdots, n_pdots, t0, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_trials(int mode, const TrialArgs &a, cudaStream_t s) {
+    long long n = (long long)a.n_periods * a.n_pdots;
+    int g = grid_for(n, 256, 4864);
+    switch (mode) {
+        case GCE_PHASE_FP64: k_trials<GCE_PHASE_FP64><<<g, 256, 0, s>>>(a); break;
+        case GCE_PHASE_SPLIT32: k_trials<GCE_PHASE_SPLIT32><<<g, 256, 0, s>>>(a); break;
+        default: k_trials<GCE_PHASE_FIXED32><<<g, 256, 0, s>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prep(int mode, const PrepArgs &a, cudaStream_t s) {
+    if (a.n_curves <= 0) return cudaSuccess;
+    switch (mode) {
+        case GCE_PHASE_FP64: k_prep<GCE_PHASE_FP64><<<a.n_curves, kPrepBlock, 0, s>>>(a); break;
+        case GCE_PHASE_SPLIT32: k_prep<GCE_PHASE_SPLIT32><<<a.n_curves, kPrepBlock, 0, s>>>(a); break;
+        default: k_prep<GCE_PHASE_FIXED32><<<a.n_curves, kPrepBlock, 0, s>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_table(unsigned long long *table, int n_max, cudaStream_t s) {
+    k_table<<<grid_for((long long)n_max + 1, 256, 1024), 256, 0, s>>>(table, n_max);
+    return cudaGetLastError();
+}
+
+}  // namespace gce

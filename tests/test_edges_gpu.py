@@ -1,0 +1,161 @@
+"""GPU edge cases, device-side input checks, determinism, graph replay and the
+host-buffer entry point."""
+import math
+
+import numpy as np
+import pytest
+import torch
+from scipy.stats import entropy as shannon
+
+import oracle
+import paper_2006_06866_gb300 as g
+import synth
+from gpu_util import dev_args, gpu_grid
+
+pytestmark = pytest.mark.gpu
+MODES = ["fp64", "split32", "fixed32"]
+
+
+@pytest.fixture(scope="module")
+def h():
+    hh = g.Handle(0)
+    yield hh
+    hh.close()
+
+
+def small_batch(seed=0, n_curves=3, n_obs=200, n_periods=300, pdots=(0.0,)):
+    rng = np.random.default_rng(seed)
+    ts = [np.sort(rng.uniform(0, 9e7, n_obs)) for _ in range(n_curves)]
+    ms = [15 + 0.3 * np.sin(2 * np.pi * t / 1234.5) + rng.normal(0, 0.05, n_obs) for t in ts]
+    offs = np.arange(n_curves + 1, dtype=np.int64) * n_obs
+    return synth.LightCurveBatch("small", np.concatenate(ts), np.concatenate(ms), offs,
+                                 synth.log_periods(300, 3000, n_periods), np.asarray(pdots), 15, 10,
+                                 np.zeros(n_curves), np.zeros(n_curves), np.zeros(n_curves))
+
+
+def test_empty_batch_is_noop(h):
+    b = small_batch()
+    args = dev_args(b)
+    args["offsets"] = np.zeros(1, dtype=np.int64)
+    out = torch.full((0, 1, b.periods.size), 7.0, device="cuda")
+    g.gce_ce_grid(h, cfg=g.Config(), out=out, **args)
+    assert g.gce_stream_status(h) == g.GCE_OK
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_degenerate_cases(h, mode):
+    """N = 1 and constant magnitudes give H = 0; one magnitude bin gives 0; one
+    phase bin gives the magnitude histogram's Shannon entropy at every trial."""
+    rng = np.random.default_rng(3)
+    t = np.sort(rng.uniform(0, 9e7, 300))
+    m = 15 + rng.normal(0, 0.1, 300)
+    parts = [(t[:1], m[:1]), (t[:50], np.full(50, 15.5)), (t, m)]
+    offs = np.concatenate([[0], np.cumsum([len(x) for x, _ in parts])]).astype(np.int64)
+    b = synth.LightCurveBatch("deg", np.concatenate([x for x, _ in parts]),
+                              np.concatenate([y for _, y in parts]), offs,
+                              synth.log_periods(300, 3000, 257), np.array([0.0, -1e-11]), 15, 10,
+                              np.zeros(3), np.zeros(3), np.zeros(3))
+    args = dev_args(b)
+    H = gpu_grid(h, args, mode)
+    assert np.all(H[0] == 0.0) and np.all(H[1] == 0.0)
+    assert np.all(gpu_grid(h, args, mode, n_mag=1) == 0.0)
+    H1 = gpu_grid(h, args, mode, n_phase=1)
+    bins = oracle.Oracle().mag_bins(m, 10)
+    expect = shannon(np.bincount(bins, minlength=10).astype(float))
+    assert np.abs(H1[2] - expect).max() <= 1e-6
+
+
+@pytest.mark.parametrize("bins", [(1, 1), (2, 3), (50, 10), (256, 255), (7, 200)])
+def test_bin_counts_range(h, bins):
+    n_phase, n_mag = bins
+    b = small_batch(seed=4, n_curves=2, n_obs=300, n_periods=130, pdots=(0.0, -2e-11))
+    args = dev_args(b)
+    got = gpu_grid(h, args, "fp64", n_phase=n_phase, n_mag=n_mag)
+    ref = oracle.Oracle().ce_grid(b.times, b.mags, b.offsets, b.periods, b.pdots, n_phase, n_mag)
+    assert np.abs(got - ref).max() <= 1e-6
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_bad_inputs_flagged_on_device(h, mode):
+    b = small_batch(seed=5)
+    for field, idx, val in [("times", 17, np.nan), ("mags", 3, np.inf), ("periods", 5, 0.0),
+                            ("periods", 9, -3.0), ("pdots", 0, np.nan)]:
+        args = dev_args(b)
+        args[field][idx] = val
+        g.gce_ce_grid(h, cfg=g.Config(15, 10, mode), **args)
+        assert g.gce_stream_status(h) == g.GCE_ERR_INVALID, (field, val)
+    # a clean call afterwards is fine again
+    g.gce_ce_grid(h, cfg=g.Config(15, 10, mode), **dev_args(b))
+    assert g.gce_stream_status(h) == g.GCE_OK
+
+
+def test_out_of_range_fold_is_unsupported(h):
+    """SPLIT32 needs |tau|/P < 2^22 cycles: 1e9 s at a 100 s period is refused."""
+    b = small_batch(seed=6, n_periods=64)
+    args = dev_args(b)
+    args["times"] = args["times"] * 12.0
+    args["periods"] = torch.full_like(args["periods"], 100.0)
+    g.gce_ce_grid(h, cfg=g.Config(15, 10, "split32"), **args)
+    assert g.gce_stream_status(h) == g.GCE_ERR_UNSUPPORTED
+    g.gce_ce_grid(h, cfg=g.Config(15, 10, "fixed32"), **args)
+    assert g.gce_stream_status(h) == g.GCE_OK
+
+
+def test_host_checks_raise(h):
+    b = small_batch()
+    args = dev_args(b)
+    args["offsets"] = np.array([0, 200, 100, 600], dtype=np.int64)
+    with pytest.raises(g.GceError):
+        g.gce_ce_grid(h, cfg=g.Config(), **args)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_deterministic_and_batch_invariant(h, mode):
+    b = small_batch(seed=7, n_curves=5, pdots=(0.0, -5e-11))
+    args = dev_args(b)
+    a1 = gpu_grid(h, args, mode)
+    a2 = gpu_grid(h, args, mode)
+    assert np.array_equal(a1, a2)
+    for c in (0, 3):
+        one = b.subset([c])
+        alone = gpu_grid(h, dev_args(one), mode)
+        assert np.array_equal(alone[0], a1[c])
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_graph_replay_with_new_inputs(h, use_graph):
+    """Same shapes, different data and buffers: the captured graph is updated, not
+    reused stale."""
+    orc = oracle.Oracle()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        for seed in (11, 12, 13):
+            b = small_batch(seed=seed, pdots=(0.0, -1e-11))
+            got = gpu_grid(h, dev_args(b), "fp64", use_graph=use_graph)
+            ref = orc.ce_grid(b.times, b.mags, b.offsets, b.periods, b.pdots, 15, 10)
+            assert np.abs(got - ref).max() <= 1e-6
+
+
+@pytest.mark.parametrize("mode", ["fp64", "fixed32"])
+def test_host_entry_point_matches_device(h, mode):
+    b = small_batch(seed=8, n_curves=4, pdots=(0.0, -2e-11))
+    cfg = g.Config(15, 10, mode)
+    dH, dI = g.gce_ce_topk(h, cfg=cfg, k=4, **dev_args(b))
+    pin = lambda a: torch.tensor(a).pin_memory()
+    hH, hI = g.gce_ce_topk_host(h, pin(b.times), pin(b.mags), b.offsets, pin(b.periods),
+                                pin(b.pdots), cfg, 4)
+    assert torch.equal(dH.cpu(), hH) and torch.equal(dI.cpu(), hI)
+    # numpy (pageable) inputs work as well
+    nH, nI = g.gce_ce_topk_host(h, b.times, b.mags, b.offsets, b.periods, b.pdots, cfg, 4)
+    assert torch.equal(nH, hH) and torch.equal(nI, hI)
+
+
+def test_autotune_keeps_results(h):
+    b = small_batch(seed=9, n_curves=2, n_obs=500, n_periods=2000)
+    cfg = g.Config(15, 10, "fixed32")
+    before = gpu_grid(h, dev_args(b), "fixed32")
+    g.gce_autotune(h, cfg, 500, 20000)
+    t = g.gce_get_tuning(h, cfg, 500)
+    assert t["block"] in (128, 256, 512) and t["tpt"] in (1, 2)
+    after = gpu_grid(h, dev_args(b), "fixed32")
+    assert np.array_equal(before, after)

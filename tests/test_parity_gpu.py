@@ -1,0 +1,222 @@
+"""GPU parity: the CUDA library (through its C ABI) against the CPU oracle on
+the same seeded inputs.  FP64 fold: bit-exact counts and |dH| <= 1e-6;
+SPLIT32 / FIXED32 folds: |dH| <= 1e-4 away from phase-bin edges."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2006_06866_gb300 as g
+import synth
+from gpu_util import EPS_PHASE, TOL_H, compare_grid, dev_args, gpu_grid, sample_cells
+
+pytestmark = pytest.mark.gpu
+MODES = ["fp64", "split32", "fixed32"]
+
+
+@pytest.fixture(scope="module")
+def h():
+    hh = g.Handle(0)
+    yield hh
+    hh.close()
+
+
+@pytest.fixture(scope="module")
+def orc():
+    return oracle.Oracle()
+
+
+def ragged_batch(seed=5):
+    """Curves of awkward lengths (1, 2, tile/chunk boundaries, long), a t0 inside
+    the baseline (so tau < 0 occurs), positive and negative Pdot."""
+    rng = np.random.default_rng(seed)
+    lengths = [1, 2, 7, 33, 100, 255, 256, 257, 1000, 2049]
+    ts, ms = [], []
+    for n in lengths:
+        t = np.sort(rng.uniform(0, 3 * 365 * 86400.0, size=n))
+        p0 = np.exp(rng.uniform(np.log(200), np.log(5000)))
+        cyc = synth.lightcurves.chirp_cycles(t, p0, -2e-11)
+        m = 15 + synth.lightcurves.eclipse_signal(cyc, 0.5, 0.05, 0.2) + rng.normal(0, 0.02, n)
+        ts.append(t)
+        ms.append(m)
+    offs = np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64)
+    periods = synth.log_periods(200.0, 5000.0, 700)
+    pdots = np.array([0.0, -3e-11, 2e-11])
+    b = synth.LightCurveBatch("ragged-test", np.concatenate(ts), np.concatenate(ms), offs, periods,
+                              pdots, 15, 10, np.zeros(len(lengths)), np.zeros(len(lengths)),
+                              np.zeros(len(lengths)), t0=4.0e7)
+    return b
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_plain_single_curve_full_grid(h, orc, mode):
+    """Workload 0 (one 100-point curve x 1000 periods) in full, every cell."""
+    b = synth.make_config(0)
+    args = dev_args(b)
+    got = gpu_grid(h, args, mode)
+    ref, dmin = orc.ce_grid(b.times, b.mags, b.offsets, b.periods, b.pdots, 15, 10, with_dmin=True)
+    compare_grid(mode, got, ref, dmin)
+    if mode == "fp64":
+        cc = np.zeros(b.periods.size, dtype=np.int64)
+        ct = np.arange(b.periods.size, dtype=np.int64)
+        cnt = g.gce_ce_counts(h, cfg=g.Config(15, 10, "fp64"), cell_curve=torch.tensor(cc, device="cuda"),
+                              cell_trial=torch.tensor(ct, device="cuda"), **args)
+        _, _, rc = orc.ce_cells(b.times, b.mags, b.offsets, b.periods, b.pdots, 15, 10, cc, ct,
+                                with_counts=True)
+        assert np.array_equal(cnt.cpu().numpy().astype(np.int64), rc)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_ragged_batch_all_cells(h, orc, mode):
+    """Ragged lengths, several trial tiles with a ragged tail, t0 mid-baseline,
+    Pdot of both signs: every cell of the grid against the oracle."""
+    b = ragged_batch()
+    args = dev_args(b)
+    got = gpu_grid(h, args, mode, t0=b.t0)
+    ref, dmin = orc.ce_grid(b.times, b.mags, b.offsets, b.periods, b.pdots, 15, 10, t0=b.t0,
+                            with_dmin=True)
+    stats = compare_grid(mode, got, ref, dmin)
+    if mode != "fp64":
+        assert stats["near_edge_frac"] < 0.05, stats
+    # counts on sampled cells: bit-exact for FP64; for the other folds equal
+    # wherever the cell is away from bin edges
+    rng = np.random.default_rng(1)
+    cc, ct = sample_cells(rng, b.n_curves, b.periods.size * b.pdots.size, 400)
+    cnt = g.gce_ce_counts(h, cfg=g.Config(15, 10, mode, t0=b.t0),
+                          cell_curve=torch.tensor(cc, device="cuda"),
+                          cell_trial=torch.tensor(ct, device="cuda"), **args)
+    _, cdmin, rc = orc.ce_cells(b.times, b.mags, b.offsets, b.periods, b.pdots, 15, 10, cc, ct,
+                                t0=b.t0, with_counts=True)
+    gc = cnt.cpu().numpy().astype(np.int64)
+    if mode == "fp64":
+        assert np.array_equal(gc, rc)
+    else:
+        far = cdmin > 4 * EPS_PHASE[mode]
+        assert np.array_equal(gc[far], rc[far])
+
+
+def test_chunked_staging_long_curves(h, orc):
+    """Curves longer than the staged chunk (forced to 256 points) give the same
+    FP64 result, bit for bit, as a single chunk, and match the oracle."""
+    b = ragged_batch(seed=9)
+    args = dev_args(b)
+    cfg = g.Config(15, 10, "fp64", t0=b.t0)
+    base = g.gce_ce_grid(h, cfg=cfg, **args).cpu().numpy()
+    g.gce_set_tuning(h, cfg, int(b.n_obs.max()), block=128, tpt=2, chunk=256)
+    try:
+        got = g.gce_ce_grid(h, cfg=cfg, **args).cpu().numpy()
+    finally:
+        g.gce_set_tuning(h, cfg, int(b.n_obs.max()), block=256, tpt=2, chunk=4096)
+    assert np.array_equal(base, got)
+    ref = orc.ce_grid(b.times, b.mags, b.offsets, b.periods, b.pdots, 15, 10, t0=b.t0)
+    assert np.abs(got - ref).max() <= TOL_H["fp64"]
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_launch_shapes_agree_bitwise(h, mode):
+    """Every launch shape gives bit-identical H (integer counts and an
+    order-independent integer entropy sum)."""
+    b = ragged_batch(seed=3)
+    args = dev_args(b)
+    cfg = g.Config(15, 10, mode, t0=b.t0)
+    n_obs = int(b.n_obs.max())
+    outs = []
+    for block in (64, 128, 256, 512):
+        for tpt in (1, 2):
+            g.gce_set_tuning(h, cfg, n_obs, block=block, tpt=tpt,
+                             chunk=4096 if mode == "fp64" else 2048)
+            outs.append(g.gce_ce_grid(h, cfg=cfg, **args).cpu().numpy())
+    g.gce_set_tuning(h, cfg, n_obs, block=256, tpt=2, chunk=4096 if mode == "fp64" else 2048)
+    for o in outs[1:]:
+        assert np.array_equal(outs[0], o)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_topk_matches_oracle(h, orc, mode):
+    b = ragged_batch(seed=4)
+    args = dev_args(b)
+    k = 5
+    cfg = g.Config(15, 10, mode, t0=b.t0)
+    tH, tI = g.gce_ce_topk(h, cfg=cfg, k=k, **args)
+    assert g.gce_stream_status(h) == g.GCE_OK
+    tH, tI = tH.cpu().numpy().astype(np.float64), tI.cpu().numpy()
+    ref = orc.ce_grid(b.times, b.mags, b.offsets, b.periods, b.pdots, 15, 10, t0=b.t0)
+    flat = ref.reshape(b.n_curves, -1)
+    grid = gpu_grid(h, args, mode, t0=b.t0).reshape(b.n_curves, -1)
+    for c in range(b.n_curves):
+        # the device top-k is exactly the k smallest of the device grid (ties by index)
+        order = np.lexsort((np.arange(grid.shape[1]), grid[c]))[:k]
+        assert np.array_equal(tI[c], order), c
+        assert np.array_equal(tH[c], grid[c, order].astype(np.float32).astype(np.float64))
+        # and agrees with the oracle's k smallest values within the tolerance
+        oref = np.sort(flat[c])[:k]
+        if mode == "fp64":
+            assert np.abs(tH[c] - oref).max() <= TOL_H["fp64"]
+            assert np.all(np.abs(flat[c, tI[c]] - tH[c]) <= TOL_H["fp64"])
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_pdot_workload_slice(h, orc, mode):
+    """Workload 2 (P-Pdot grid): 2 curves x 500 periods x all 256 Pdot values."""
+    b = synth.make_config(2).subset([0, 1], periods=synth.make_config(2).periods[::20])
+    args = dev_args(b)
+    got = gpu_grid(h, args, mode)
+    ref, dmin = orc.ce_grid(b.times, b.mags, b.offsets, b.periods, b.pdots, 15, 10, with_dmin=True)
+    compare_grid(mode, got, ref, dmin)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_longbase_workload_slice(h, orc, mode):
+    """Workload 4 (10-yr baseline, 20 phase bins): 2 curves x 1000 periods x 64 Pdot."""
+    full = synth.make_config(4)
+    b = full.subset([0, 1], periods=full.periods[::100])
+    args = dev_args(b)
+    got = gpu_grid(h, args, mode, n_phase=20)
+    ref, dmin = orc.ce_grid(b.times, b.mags, b.offsets, b.periods, b.pdots, 20, 10, with_dmin=True)
+    compare_grid(mode, got, ref, dmin)
+
+
+@pytest.mark.parametrize("mode", ["split32", "fixed32"])
+def test_injected_argmin_matches(h, orc, mode):
+    """On-grid injected chirping eclipses: the reduced-precision folds find the
+    oracle's argmin cell (tie sets compared)."""
+    periods = synth.log_periods(180.0, 900.0, 400)
+    pdots = np.linspace(-1e-10, 0.0, 32)
+    b, pi, qi = synth.make_onegrid_injection(77, 8, 500, periods, pdots, noise=0.02)
+    args = dev_args(b)
+    got = gpu_grid(h, args, mode).reshape(b.n_curves, -1)
+    ref = orc.ce_grid(b.times, b.mags, b.offsets, b.periods, b.pdots, 15, 10).reshape(b.n_curves, -1)
+    for c in range(b.n_curves):
+        ties = np.flatnonzero(ref[c] <= ref[c].min() + 1e-12)
+        assert int(np.argmin(got[c])) in ties, c
+        assert int(qi[c] * periods.size + pi[c]) in ties, c
+
+
+def test_single_launch_baseline_matches_batched(h, orc):
+    b = ragged_batch(seed=6)
+    args = dev_args(b)
+    cfg = g.Config(15, 10, "fp64", t0=b.t0)
+    a = g.gce_ce_grid(h, cfg=cfg, **args).cpu().numpy()
+    s = g.gce_ce_grid_single(h, cfg=cfg, **args).cpu().numpy()
+    assert np.array_equal(a, s)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_full_size_batch_sampled(h, orc, mode):
+    """Workload 1 at full size (1000 curves x 1000 obs x 1e5 periods) in the
+    benchmark's launch configuration; 300 sampled cells against the oracle."""
+    b = synth.make_config(1)
+    args = dev_args(b)
+    got = gpu_grid(h, args, mode)
+    rng = np.random.default_rng(2)
+    cc, ct = sample_cells(rng, b.n_curves, b.periods.size, 300)
+    rh, rd, _ = orc.ce_cells(b.times, b.mags, b.offsets, b.periods, b.pdots, 15, 10, cc, ct)
+    gv = got.reshape(b.n_curves, -1)[cc, ct]
+    err = np.abs(gv - rh)
+    if mode == "fp64":
+        assert err.max() <= 1e-6
+    else:
+        far = rd > 4 * EPS_PHASE[mode]
+        assert err[far].max() <= 1e-4
+    # property at every cell: 0 <= H <= ln(n_mag)
+    assert float(got.min()) >= 0.0 and float(got.max()) <= np.log(10) + 1e-6
