@@ -51,6 +51,9 @@ def parse():
                     help="skip the FP64 / SPLIT32 / one-launch-per-curve comparison legs")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU seconds of the oracle baseline sample")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--curves", type=int, default=0,
+                    help="use only the first N curves of the workload (profiling runs)")
     return ap.parse_args()
 
 
@@ -115,7 +118,7 @@ def run_reference(args, rank, world):
     used = 1
     desc = ""
     for s in range(args.warmup + args.steps):
-        r, used, desc = oracle_rate(batch, per_step)
+        r, used, desc = oracle_rate(batch, per_step, n_threads=os.cpu_count() or 1)
         if s >= args.warmup:
             rates.append(r)
     value = float(np.median(rates))
@@ -212,6 +215,8 @@ def main():
             pg.barrier()
 
     batch = synth.make_config(args.workload)
+    if args.curves:
+        batch = batch.subset(list(range(min(args.curves, batch.n_curves))))
     k = batch.topk or 5
     pt_step = batch.point_trials
     t_d = torch.tensor(batch.times, device=dev)
@@ -323,9 +328,9 @@ def main():
         extras["speedup_vs_fp64_single_launch"] = value / world / extras["fp64_single_launch"]["value"]
 
     cpu = None
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and not args.no_cpu:
         try:
-            r, used, desc = oracle_rate(batch, args.cpu_seconds)
+            r, used, desc = oracle_rate(batch, args.cpu_seconds, n_threads=os.cpu_count() or 1)
             cpu = {"value": r, "unit": UNIT, "cores": used, "kind": "oracle", "sample": desc,
                    "cpu": cpu_model()}
         except Exception as e:  # the baseline is context; never fail the bench on it

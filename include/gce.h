@@ -59,8 +59,9 @@ typedef enum {
      * evaluation of that sequence. */
     GCE_PHASE_FP64 = 0,
     /* FP32 double-float: tau, tau^2, f and a split into (hi, lo) float pairs,
-     * error-free products via fmaf, integer cycles removed with rintf.  Phase
-     * error about 1e-7 cycles; needs |tau|/P < 2^22 cycles. */
+     * error-free products via fmaf, integer cycles removed with a rounding
+     * constant.  Phase error about 1e-7 cycles; needs |tau|/P < 2^21 and
+     * |Pdot| tau^2/(2 P^2) < 2^19 cycles. */
     GCE_PHASE_SPLIT32 = 1,
     /* fixed point: tau, tau^2, f and a as 64-bit integers split into 32-bit
      * limbs; the phase is the low 32 bits of their products (integer cycles wrap

@@ -272,18 +272,21 @@ gce_status make_plan(gce_handle h, const Job &j, Plan &pl) {
     pl.chunk = std::min(t.chunk, ((pl.n_max + 31) / 32) * 32);
     pl.table_smem = std::min(pl.n_max + 1, 2048);
     const int kk = j.kind == JOB_TOPK ? j.k : 0;
-    pl.smem = main_smem_bytes(cfg->phase_mode, pl.block, pl.tpt, pl.chunk, cfg->n_phase_bins,
-                              cfg->n_mag_bins, pl.table_smem, kk);
-    // shrink the staged chunk (then the table) until the CTA fits
-    while (pl.smem > (size_t)h->smem_optin && pl.chunk > 256) {
-        pl.chunk = std::max(256, pl.chunk / 2);
-        pl.smem = main_smem_bytes(cfg->phase_mode, pl.block, pl.tpt, pl.chunk, cfg->n_phase_bins,
-                                  cfg->n_mag_bins, pl.table_smem, kk);
-    }
-    while (pl.smem > (size_t)h->smem_optin && pl.table_smem > 64) {
-        pl.table_smem /= 2;
-        pl.smem = main_smem_bytes(cfg->phase_mode, pl.block, pl.tpt, pl.chunk, cfg->n_phase_bins,
-                                  cfg->n_mag_bins, pl.table_smem, kk);
+    // shrink the staged chunk, then the table, then trials per thread, then the
+    // block, until the CTA fits in shared memory
+    auto size = [&]() {
+        return main_smem_bytes(cfg->phase_mode, pl.block, pl.tpt, pl.chunk, cfg->n_phase_bins,
+                               cfg->n_mag_bins, pl.table_smem, kk);
+    };
+    pl.smem = size();
+    while (pl.smem > (size_t)h->smem_optin) {
+        if (pl.chunk > 512) pl.chunk /= 2;
+        else if (pl.table_smem > 256) pl.table_smem /= 2;
+        else if (pl.tpt > 1) pl.tpt = 1;
+        else if (pl.block > 64) pl.block /= 2;
+        else if (pl.chunk > 64) pl.chunk /= 2;
+        else break;
+        pl.smem = size();
     }
     if (pl.smem > (size_t)h->smem_optin)
         return fail(h, GCE_ERR_UNSUPPORTED, "launch shape needs %zu bytes of shared memory", pl.smem);

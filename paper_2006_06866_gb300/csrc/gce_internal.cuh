@@ -111,31 +111,37 @@ __device__ __forceinline__ int fold_fp64(double tau, double f, double a, double 
 
 // Eq. 3 in FP32 double-float.  tau f = th fh + (th fl + tl fh) (+ tl fl, below
 // 2^-48 relative): p = RN(th fh) with its exact error e = fma(th, fh, -p)
-// (Dekker's product via FMA); the integer cycles of p are removed exactly with
-// rintf; the small cross terms are added to e.  The Pdot term a tau^2 is
-// treated the same way with tau^2 = t2h + t2l and a = ah + al.
+// (Dekker's product via FMA); the integer cycles of p are removed exactly by
+// the 1.5 2^23 rounding constant (|p| < 2^21 cycles, checked per job); the
+// small cross terms join e.  The Pdot term a tau^2 is treated the same way
+// with tau^2 = t2h + t2l and a = ah + al.  x = r + c then lies in (-1, 1), and
+// one round-down FMA against the same constant gives n_phase + floor(x
+// n_phase) in [0, 2 n_phase): the returned slot, where slots j and
+// j + n_phase both stand for phase bin j (so no modulo is needed here).
+constexpr float kRound = 12582912.0f;  // 1.5 * 2^23
+
 template <bool PDOT>
-__device__ __forceinline__ int fold_split(float4 pt, float4 tr, float nphi, int n_phase) {
+__device__ __forceinline__ int fold_split(float4 pt, float4 tr, float nphi, float zoff) {
     const float th = pt.x, tl = pt.y;
     const float fh = tr.x, fl = tr.y;
     float p = __fmul_rn(th, fh);
     float e = __fmaf_rn(th, fh, -p);
-    float r = __fsub_rn(p, rintf(p));
+    float r = __fsub_rn(p, __fsub_rn(__fadd_rn(p, kRound), kRound));
     float c = __fmaf_rn(th, fl, __fmaf_rn(tl, fh, e));
     if (PDOT) {
         const float t2h = pt.z, t2l = pt.w;
         const float ah = tr.z, al = tr.w;
         float q = __fmul_rn(ah, t2h);
         float e2 = __fmaf_rn(ah, t2h, -q);
-        float r2 = __fsub_rn(q, rintf(q));
+        float r2 = __fsub_rn(q, __fsub_rn(__fadd_rn(q, kRound), kRound));
         float c2 = __fmaf_rn(al, t2h, __fmaf_rn(ah, t2l, e2));
-        r = __fsub_rn(r, r2);
+        float d = __fsub_rn(r, r2);
+        r = __fsub_rn(d, __fsub_rn(__fadd_rn(d, kRound), kRound));
         c = __fsub_rn(c, c2);
     }
-    float x = __fadd_rn(r, c);
-    float ph = __fsub_rn(x, floorf(x));
-    int j = __float2int_rz(__fmul_rn(ph, nphi));
-    return min(j, n_phase - 1);
+    const float x = __fadd_rn(r, c);
+    const float z = __fmaf_rd(x, nphi, zoff);  // zoff = 1.5 2^23 + n_phase
+    return __float_as_int(z) - __float_as_int(kRound);
 }
 
 // Eq. 3 in 32-bit-limb fixed point.  With T = T1 2^32 + T0 and F = F1 2^32 + F0
@@ -166,6 +172,9 @@ __device__ __forceinline__ int fold_fixed(uint4 pt, uint4 tr, unsigned int n_pha
 }
 
 // ------------------------------------------------------------------ entropy
+
+// Phase-bin slots per trial in the counters: SPLIT32 uses two per bin.
+__host__ __device__ constexpr int slots_per_bin(int mode) { return mode == GCE_PHASE_SPLIT32 ? 2 : 1; }
 
 // Fixed-point table of c ln c: tab[c] = round(c ln(c) 2^32), tab[0] = tab[1] = 0.
 // Eq. 4 rewritten with integer counts is
@@ -229,6 +238,7 @@ cudaError_t launch_prep(int mode, const PrepArgs &a, cudaStream_t s);
 cudaError_t launch_table(unsigned long long *table, int n_max, cudaStream_t s);
 size_t main_smem_bytes(int mode, int block, int tpt, int chunk, int n_phase, int n_mag,
                        int table_smem, int k);
+size_t single_smem_bytes(int n_phase, int block);
 cudaError_t main_kernel_attrs(int mode, int tpt, size_t smem);
 const void *main_kernel_ptr(int mode, int tpt);
 cudaError_t launch_main(int mode, int tpt, int block, int grid, size_t smem,

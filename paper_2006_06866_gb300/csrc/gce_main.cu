@@ -9,9 +9,15 @@
 // bin during preparation, are staged in shared memory and read by every thread
 // as broadcasts.  Because the points arrive one magnitude bin at a time, each
 // thread needs only a 1-D phase histogram per trial (the paper's
-// 1/n_mag-memory observation): counters are cumulative u16 [trial][phase bin]
-// arrays private to the thread, and at the end of each magnitude segment the
-// difference against a snapshot gives that segment's c_ij.
+// 1/n_mag-memory observation).
+//
+// Counters.  One 32-bit shared-memory word per (trial, phase slot), private to
+// its thread and laid out [trial][slot][thread] so a warp's accesses fall in
+// distinct banks.  The low 16 bits count points (N <= 65535); the high 16 bits
+// hold a snapshot taken at the end of the previous magnitude segment, so the
+// segment's c_ij is low - high.  Points are counted with a shared-memory atomic
+// add whose result is unused: it needs no read-modify-write round trip in the
+// thread, and no other thread touches the word.
 //
 // Entropy.  N H = sum_j c_j ln c_j - sum_ij c_ij ln c_ij, accumulated as exact
 // 64-bit integers from a fixed-point c ln c table (2^32 scale); H is converted
@@ -43,20 +49,37 @@ __device__ __forceinline__ unsigned long long tab_lookup(const unsigned long lon
     return c < table_smem ? s_tab[c] : __ldg(g_tab + c);
 }
 
+// Per-mode constants of the fold, computed once per kernel.
+struct FoldConst {
+    double nphi_d;
+    float nphi_f;
+    float zoff;     // SPLIT32: 1.5 2^23 + n_phase
+    int n_phase;
+};
+
+__device__ __forceinline__ FoldConst fold_const(int n_phase) {
+    FoldConst k;
+    k.nphi_d = (double)n_phase;
+    k.nphi_f = (float)n_phase;
+    k.zoff = kRound + (float)n_phase;
+    k.n_phase = n_phase;
+    return k;
+}
+
+// Fold<MODE>::slot returns the counter slot of a point for a trial: the phase
+// bin (FP64, FIXED32) or the bin plus 0 or n_phase (SPLIT32, two slots per bin).
 template <int MODE> struct Fold;
 template <> struct Fold<GCE_PHASE_FP64> {
     template <bool PDOT>
-    __device__ __forceinline__ static int bin(double p, double2 t, double nphi_d, float,
-                                              int n_phase) {
-        return fold_fp64<PDOT>(p, t.x, t.y, nphi_d, n_phase);
+    __device__ __forceinline__ static int slot(double p, double2 t, const FoldConst &k) {
+        return fold_fp64<PDOT>(p, t.x, t.y, k.nphi_d, k.n_phase);
     }
     __device__ __forceinline__ static bool has_pdot(double2 t) { return t.y != 0.0; }
 };
 template <> struct Fold<GCE_PHASE_SPLIT32> {
     template <bool PDOT>
-    __device__ __forceinline__ static int bin(float4 p, float4 t, double, float nphi_f,
-                                              int n_phase) {
-        return fold_split<PDOT>(p, t, nphi_f, n_phase);
+    __device__ __forceinline__ static int slot(float4 p, float4 t, const FoldConst &k) {
+        return fold_split<PDOT>(p, t, k.nphi_f, k.zoff);
     }
     __device__ __forceinline__ static bool has_pdot(float4 t) {
         return t.z != 0.0f || t.w != 0.0f;
@@ -64,8 +87,8 @@ template <> struct Fold<GCE_PHASE_SPLIT32> {
 };
 template <> struct Fold<GCE_PHASE_FIXED32> {
     template <bool PDOT>
-    __device__ __forceinline__ static int bin(uint4 p, uint4 t, double, float, int n_phase) {
-        return fold_fixed<PDOT>(p, t, (unsigned int)n_phase);
+    __device__ __forceinline__ static int slot(uint4 p, uint4 t, const FoldConst &k) {
+        return fold_fixed<PDOT>(p, t, (unsigned int)k.n_phase);
     }
     __device__ __forceinline__ static bool has_pdot(uint4 t) { return (t.z | t.w) != 0u; }
 };
@@ -75,22 +98,30 @@ template <> struct Fold<GCE_PHASE_FIXED32> {
 template <int MODE, int TPT, bool PDOT>
 __device__ __forceinline__ void count_points(
     const typename ModeTraits<MODE>::point_t *__restrict__ pts, int ka, int kb,
-    const typename ModeTraits<MODE>::trial_t (&tc)[TPT], unsigned short *cnt, int stride_j,
-    int stride_s, double nphi_d, float nphi_f, int n_phase) {
-#pragma unroll 2
+    const typename ModeTraits<MODE>::trial_t (&tc)[TPT], unsigned int *cnt, int stride_j,
+    int stride_s, const FoldConst &fk) {
+#pragma unroll 4
     for (int k = ka; k < kb; ++k) {
         const typename ModeTraits<MODE>::point_t p = pts[k];
 #pragma unroll
         for (int s = 0; s < TPT; ++s) {
-            const int j = Fold<MODE>::template bin<PDOT>(p, tc[s], nphi_d, nphi_f, n_phase);
-            unsigned short *cp = cnt + s * stride_s + j * stride_j;
-            *cp = (unsigned short)(*cp + 1);
+            const int j = Fold<MODE>::template slot<PDOT>(p, tc[s], fk);
+            atomicAdd(cnt + s * stride_s + j * stride_j, 1u);
         }
     }
 }
 
+// c_ij of one phase bin at the end of a magnitude segment (low - snapshot), with
+// the snapshot moved up to the current count.
+__device__ __forceinline__ int take_segment(unsigned int *w) {
+    const unsigned int v = *w;
+    const unsigned int cur = v & 0xffffu;
+    *w = cur * 0x10001u;
+    return (int)(cur - (v >> 16));
+}
+
 template <int MODE, int TPT>
-__global__ void __launch_bounds__(512, 1) k_main(MainArgs a) {
+__global__ void __launch_bounds__(512, 2) k_main(MainArgs a) {
     typedef typename ModeTraits<MODE>::point_t point_t;
     typedef typename ModeTraits<MODE>::trial_t trial_t;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -100,13 +131,14 @@ __global__ void __launch_bounds__(512, 1) k_main(MainArgs a) {
 
     const int B = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n_phase = a.n_phase, n_mag = a.n_mag;
-    const int stride_j = B, stride_s = n_phase * B;
+    constexpr int SPB = slots_per_bin(MODE);
+    const int n_slots = SPB * n_phase;
+    const int stride_j = B, stride_s = n_slots * B;
 
     point_t *s_pts = reinterpret_cast<point_t *>(smem);
     unsigned long long *s_tab = reinterpret_cast<unsigned long long *>(s_pts + a.chunk);
-    unsigned short *s_cnt = reinterpret_cast<unsigned short *>(s_tab + a.table_smem);
-    unsigned short *s_prev = s_cnt + TPT * n_phase * B;
-    int *s_seg = reinterpret_cast<int *>(s_prev + TPT * n_phase * B);
+    unsigned int *s_cnt = reinterpret_cast<unsigned int *>(s_tab + a.table_smem);
+    int *s_seg = reinterpret_cast<int *>(s_cnt + TPT * n_slots * B);
     unsigned long long *s_top =
         reinterpret_cast<unsigned long long *>(s_seg + ((n_mag + 2) & ~1));
 
@@ -114,10 +146,8 @@ __global__ void __launch_bounds__(512, 1) k_main(MainArgs a) {
 
     const point_t *g_pts = reinterpret_cast<const point_t *>(a.payload);
     const trial_t *g_tr = reinterpret_cast<const trial_t *>(a.trialc);
-    const double nphi_d = (double)n_phase;
-    const float nphi_f = (float)n_phase;
-    unsigned short *my_cnt = s_cnt + tid;
-    unsigned short *my_prev = s_prev + tid;
+    const FoldConst fk = fold_const(n_phase);
+    unsigned int *my_cnt = s_cnt + tid;
 
     int staged_curve = -1, staged_lo = -1;
     long long item = 0, item_end = 0;
@@ -157,10 +187,7 @@ __global__ void __launch_bounds__(512, 1) k_main(MainArgs a) {
         }
         const bool pdot = __syncthreads_or(any_pdot) != 0;
 
-        for (int i = 0; i < TPT * n_phase; ++i) {
-            my_cnt[i * B] = 0;
-            my_prev[i * B] = 0;
-        }
+        for (int i = 0; i < TPT * n_slots; ++i) my_cnt[i * B] = 0u;
         unsigned long long s_ij[TPT];
 #pragma unroll
         for (int s = 0; s < TPT; ++s) s_ij[s] = 0ull;
@@ -179,22 +206,21 @@ __global__ void __launch_bounds__(512, 1) k_main(MainArgs a) {
                 const int ka = max(s0, lo), kb = min(s1, hi);
                 if (ka < kb) {
                     if (pdot)
-                        count_points<MODE, TPT, true>(s_pts - lo, ka, kb, tc, my_cnt, stride_j,
-                                                      stride_s, nphi_d, nphi_f, n_phase);
+                        count_points<MODE, TPT, true>(s_pts, ka - lo, kb - lo, tc, my_cnt,
+                                                      stride_j, stride_s, fk);
                     else
-                        count_points<MODE, TPT, false>(s_pts - lo, ka, kb, tc, my_cnt, stride_j,
-                                                       stride_s, nphi_d, nphi_f, n_phase);
+                        count_points<MODE, TPT, false>(s_pts, ka - lo, kb - lo, tc, my_cnt,
+                                                       stride_j, stride_s, fk);
                 }
                 if (s1 > s0 && s1 > lo && s1 <= hi) {
                     // end of magnitude segment i: c_ij = counter - snapshot
 #pragma unroll
                     for (int s = 0; s < TPT; ++s) {
                         unsigned long long acc = 0ull;
+                        unsigned int *w = my_cnt + s * stride_s;
                         for (int j = 0; j < n_phase; ++j) {
-                            const int o = s * stride_s + j * stride_j;
-                            const int cur = my_cnt[o];
-                            const int cij = cur - (int)my_prev[o];
-                            my_prev[o] = (unsigned short)cur;
+                            int cij = take_segment(w + j * stride_j);
+                            if (SPB == 2) cij += take_segment(w + (j + n_phase) * stride_j);
                             acc += tab_lookup(s_tab, a.table_smem, a.table, cij);
                         }
                         s_ij[s] += acc;
@@ -209,8 +235,12 @@ __global__ void __launch_bounds__(512, 1) k_main(MainArgs a) {
 #pragma unroll
         for (int s = 0; s < TPT; ++s) {
             unsigned long long sj = 0ull;
-            for (int j = 0; j < n_phase; ++j)
-                sj += tab_lookup(s_tab, a.table_smem, a.table, my_cnt[s * stride_s + j * stride_j]);
+            const unsigned int *w = my_cnt + s * stride_s;
+            for (int j = 0; j < n_phase; ++j) {
+                int cj = (int)(w[j * stride_j] & 0xffffu);
+                if (SPB == 2) cj += (int)(w[(j + n_phase) * stride_j] & 0xffffu);
+                sj += tab_lookup(s_tab, a.table_smem, a.table, cj);
+            }
             long long d = (long long)(sj - s_ij[s]);
             if (d < 0) d = 0;
             const float h = __double2float_rn(__dmul_rn(__ll2double_rn(d), inv));
@@ -294,34 +324,26 @@ __global__ void __launch_bounds__(256) k_single(MainArgs a, int c) {
     if (a.state->err) return;
     const int B = blockDim.x, tid = threadIdx.x;
     const int n_phase = a.n_phase, n_mag = a.n_mag;
-    unsigned short *cnt = reinterpret_cast<unsigned short *>(smem) + tid;
-    unsigned short *prev = cnt + n_phase * B;
+    unsigned int *cnt = reinterpret_cast<unsigned int *>(smem) + tid;
     const long long t = (long long)blockIdx.x * B + tid;
     const bool valid = t < a.n_trials;
     const double2 tr = valid ? reinterpret_cast<const double2 *>(a.trialc)[t] : double2{0.0, 0.0};
     const double *pts = reinterpret_cast<const double *>(a.payload) + a.offsets[c];
     const int *seg = a.seg + (long long)c * (n_mag + 1);
     const int n = (int)(a.offsets[c + 1] - a.offsets[c]);
-    for (int j = 0; j < n_phase; ++j) {
-        cnt[j * B] = 0;
-        prev[j * B] = 0;
-    }
+    for (int j = 0; j < n_phase; ++j) cnt[j * B] = 0u;
     unsigned long long s_ij = 0ull;
     for (int i = 0; i < n_mag; ++i) {
         const int s0 = seg[i], s1 = seg[i + 1];
         if (s1 == s0) continue;
         for (int k = s0; k < s1; ++k) {
             const int j = fold_fp64<true>(__ldg(pts + k), tr.x, tr.y, (double)n_phase, n_phase);
-            cnt[j * B] = (unsigned short)(cnt[j * B] + 1);
+            atomicAdd(cnt + j * B, 1u);
         }
-        for (int j = 0; j < n_phase; ++j) {
-            const int cur = cnt[j * B];
-            s_ij += __ldg(a.table + (cur - prev[j * B]));
-            prev[j * B] = (unsigned short)cur;
-        }
+        for (int j = 0; j < n_phase; ++j) s_ij += __ldg(a.table + take_segment(cnt + j * B));
     }
     unsigned long long sj = 0ull;
-    for (int j = 0; j < n_phase; ++j) sj += __ldg(a.table + cnt[j * B]);
+    for (int j = 0; j < n_phase; ++j) sj += __ldg(a.table + (cnt[j * B] & 0xffffu));
     long long d = (long long)(sj - s_ij);
     if (d < 0) d = 0;
     if (valid)
@@ -344,12 +366,12 @@ __global__ void k_counts(MainArgs a, long long n_cells, const long long *cell_cu
     const int *seg = a.seg + c * (a.n_mag + 1);
     unsigned int *out = counts + cell * a.n_mag * a.n_phase;
     const bool pdot = Fold<MODE>::has_pdot(tr);
+    const FoldConst fk = fold_const(a.n_phase);
     for (int i = 0; i < a.n_mag; ++i) {
         for (int k = seg[i]; k < seg[i + 1]; ++k) {
-            const int j = pdot ? Fold<MODE>::template bin<true>(pts[k], tr, (double)a.n_phase,
-                                                                (float)a.n_phase, a.n_phase)
-                               : Fold<MODE>::template bin<false>(pts[k], tr, (double)a.n_phase,
-                                                                 (float)a.n_phase, a.n_phase);
+            int j = pdot ? Fold<MODE>::template slot<true>(pts[k], tr, fk)
+                         : Fold<MODE>::template slot<false>(pts[k], tr, fk);
+            if (j >= a.n_phase) j -= a.n_phase;  // SPLIT32's second slot of a bin
             out[i * a.n_phase + j] += 1u;
         }
     }
@@ -367,10 +389,12 @@ size_t main_smem_bytes(int mode, int block, int tpt, int chunk, int n_phase, int
                        int table_smem, int k) {
     size_t pt = mode == GCE_PHASE_FP64 ? 8 : 16;
     size_t b = pt * (size_t)chunk + 8 * (size_t)table_smem +
-               2 * 2 * (size_t)tpt * n_phase * block + 4 * (size_t)((n_mag + 2) & ~1) +
-               8 * (size_t)(block / 32) * (size_t)(k > 0 ? k : 1);
+               4 * (size_t)tpt * slots_per_bin(mode) * n_phase * block +
+               4 * (size_t)((n_mag + 2) & ~1) + 8 * (size_t)(block / 32) * (size_t)(k > 0 ? k : 1);
     return b;
 }
+
+size_t single_smem_bytes(int n_phase, int block) { return 4 * (size_t)n_phase * block; }
 
 const void *main_kernel_ptr(int mode, int tpt) {
     switch (mode * 4 + tpt) {
@@ -412,9 +436,11 @@ cudaError_t launch_topk_merge(const unsigned long long *cand, int n_curves, int 
 }
 
 cudaError_t launch_single(const MainArgs &a, int curve, long long, cudaStream_t s) {
-    const int B = 256;
+    // the largest power-of-two block (<= 256) whose counters fit in 48 KB
+    int B = 256;
+    while (B > 32 && single_smem_bytes(a.n_phase, B) > 48 * 1024) B >>= 1;
     const long long g = (a.n_trials + B - 1) / B;
-    const size_t smem = 2 * 2 * (size_t)a.n_phase * B;
+    const size_t smem = single_smem_bytes(a.n_phase, B);
     k_single<<<(unsigned int)g, B, smem, s>>>(a, curve);
     return cudaGetLastError();
 }

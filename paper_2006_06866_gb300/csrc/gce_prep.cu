@@ -94,7 +94,8 @@ __global__ void k_trials(TrialArgs a) {
             const double amax = 0.5 * dmax * fmax_ * fmax_;
             bool bad = false;
             if (MODE == GCE_PHASE_SPLIT32) {
-                bad = tau_max * fmax_ >= 4194304.0 || amax * tau_max * tau_max >= 4194304.0;
+                // |x| < 1 needs |c| + |c2| < 1/2: cycles < 2^21 and Pdot cycles < 2^19
+                bad = tau_max * fmax_ >= 2097152.0 || amax * tau_max * tau_max >= 524288.0;
             } else if (MODE == GCE_PHASE_FIXED32) {
                 bad = ldexp(fmax_, fs.e_tau) >= 536870912.0 ||
                       ldexp(amax, 2 * fs.e_tau) >= 536870912.0;
