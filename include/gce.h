@@ -65,8 +65,10 @@ typedef enum {
     GCE_PHASE_SPLIT32 = 1,
     /* fixed point: tau, tau^2, f and a as 64-bit integers split into 32-bit
      * limbs; the phase is the low 32 bits of their products (integer cycles wrap
-     * away), so the fold is integer multiply-high work.  Phase error a few
-     * 2^-32 cycles; needs |tau|/P < 2^28 and |Pdot| tau^2/P^2 < 2^28 cycles. */
+     * away).  The large partial products are integer multiplies, the small
+     * cross terms FP32 multiply-adds.  Phase error a few 2^-32 cycles up to
+     * about 2^22 cycles, growing to ~6e-8 cycles at the limit; needs |tau|/P <
+     * 2^28 and |Pdot| tau^2/P^2 < 2^16 cycles. */
     GCE_PHASE_FIXED32 = 2
 } gce_phase_mode;
 

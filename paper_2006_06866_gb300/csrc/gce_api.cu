@@ -426,7 +426,7 @@ gce_status run_job(gce_handle h, const Job &j, cudaStream_t s) {
     // workspace
     if ((st = ensure(h, h->payload, (size_t)point_bytes(mode) * pl.n_points)) != GCE_OK) return st;
     if ((st = ensure(h, h->seg, sizeof(int) * (size_t)j.n_curves * (j.cfg->n_mag_bins + 1))) != GCE_OK) return st;
-    if ((st = ensure(h, h->trialc, 16 * (size_t)pl.n_trials)) != GCE_OK) return st;
+    if ((st = ensure(h, h->trialc, 32 * (size_t)pl.n_trials)) != GCE_OK) return st;
     if ((st = ensure(h, h->order, sizeof(int) * (size_t)j.n_curves)) != GCE_OK) return st;
     if ((st = ensure(h, h->offsets, sizeof(long long) * (size_t)(j.n_curves + 1))) != GCE_OK) return st;
     if (j.kind == JOB_TOPK &&

@@ -62,11 +62,18 @@ __host__ __device__ inline FixedScale fixed_scale_from(double tau_max) {
 // Per point, sorted by magnitude bin, in the layout of the fold mode.
 //   FP64:    double tau                                        (8 bytes)
 //   SPLIT32: float4 {tau_hi, tau_lo, tau2_hi, tau2_lo}          (16 bytes)
-//   FIXED32: uint4  {T1 (int32), T0, U1, U0 (int32, balanced)}  (16 bytes)
+//   FIXED32: uint4  {T1 (int32), t0f, U1, u0f}                  (16 bytes)
+//            T = tau 2^s = T1 2^32 + T0; U = tau^2 2^u = U1 2^32 + U0 (U0
+//            balanced); t0f, u0f are the bit patterns of the floats
+//            2^23 + (T0 >> 9) and 2^23 + ((U0 + 2^31) >> 9).
 // Per flat trial:
 //   FP64:    double2 {f, a}
 //   SPLIT32: float4  {f_hi, f_lo, a_hi, a_lo}
-//   FIXED32: uint4   {F1, F0 (int32, balanced), An1 (int32), An0} with An = -A
+//   FIXED32: FixedTrial, see fold_fixed.
+struct FixedTrial {
+    uint4 i;   // {F1, F0 (int32, balanced), A1 (int32), A0}: F = f 2^r, A = -a 2^v
+    float4 f;  // {G0, G2, K, k as bits}: the FP32 cross terms' scales and offset
+};
 template <int MODE> struct ModeTraits;
 template <> struct ModeTraits<GCE_PHASE_FP64> {
     typedef double point_t;
@@ -78,7 +85,7 @@ template <> struct ModeTraits<GCE_PHASE_SPLIT32> {
 };
 template <> struct ModeTraits<GCE_PHASE_FIXED32> {
     typedef uint4 point_t;
-    typedef uint4 trial_t;
+    typedef FixedTrial trial_t;
 };
 
 // Balanced split of a 64-bit value: x = hi 2^32 + lo with lo a signed 32-bit
@@ -144,31 +151,80 @@ __device__ __forceinline__ int fold_split(float4 pt, float4 tr, float nphi, floa
     return __float_as_int(z) - __float_as_int(kRound);
 }
 
-// Eq. 3 in 32-bit-limb fixed point.  With T = T1 2^32 + T0 and F = F1 2^32 + F0
-// (F0 balanced), bits 64..95 of T F -- the phase in units of 2^-32 cycles, the
-// integer cycles having wrapped out of the 32-bit word -- are
-//   lo32(T1 F1) + hi32(T1 F0) + hi32(T0 F1)     (dropped carries: -1..+2 units).
-// The Pdot term is the same product for U (tau^2) and An = -A (a); then the
-// phase bin is floor(phase n_phase / 2^32) = hi32(phase n_phase).
+// Eq. 3 in 32-bit-limb fixed point, the phase in units of 2^-32 cycles so that
+// the integer cycles wrap out of a 32-bit word.  With T = T1 2^32 + T0 and
+// F = F1 2^32 + F0, bits 64..95 of T F are
+//   lo32(T1 F1) + hi32(T1 F0) + T0 F1 / 2^32            (+ dropped carries).
+// The first two are exact integer products (IMAD, IMAD.HI).  The third is
+// below g1 = F1 units and is computed on the FP32 pipe: t0f = 2^23 + (T0 >> 9)
+// times G0 = F1 2^(-23-k), added to an offset K that removes the 2^23 G0
+// term and carries the 1.5 2^23 rounding constant, so the FMA result's bit
+// pattern holds the term rounded to 2^k units (k per trial, the smallest with
+// F1 < 2^(22+k)); it joins the accumulator shifted left by k, and the integer
+// offset C = -(bits(1.5 2^23) << k) cancels the constant's bits.  The Pdot term
+// -a tau^2 is the same construction for U and A = -a 2^v: lo32(U1 A1) and
+// hi32(A0 U1) exact, hi32(A1 U0) through u0f and G2 in the same FMA chain.
+// Error: dropped carries (-1..+2 units), T0 >> 9 truncation (<= F1 2^-23),
+// FP32 roundings (<= 3 2^(k-1)), so a few 2^-32 cycles for k <= 2.
+// The phase bin is floor(phase n_phase / 2^32) = hi32(phase n_phase).
+__device__ __forceinline__ unsigned int mad_lo_u32(unsigned int a, unsigned int b,
+                                                   unsigned int c) {
+    unsigned int d;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+__device__ __forceinline__ unsigned int mad_hi_s32(int a, int b, unsigned int c) {
+    int d;
+    asm("mad.hi.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"((int)c));
+    return (unsigned int)d;
+}
+__device__ __forceinline__ unsigned int mad_hi_u32(unsigned int a, unsigned int b,
+                                                   unsigned int c) {
+    unsigned int d;
+    asm("mad.hi.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+
+// Per-trial values of the FIXED32 fold that stay in registers.
+struct FixedPrep {
+    unsigned int F1, A1, A0, C, k;
+    int F0;
+    float G0, G2, K;
+};
+
+__device__ __forceinline__ FixedPrep fixed_prep(const FixedTrial &t) {
+    FixedPrep p;
+    p.F1 = t.i.x;
+    p.F0 = (int)t.i.y;
+    p.A1 = t.i.z;
+    p.A0 = t.i.w;
+    p.G0 = t.f.x;
+    p.G2 = t.f.y;
+    p.K = t.f.z;
+    p.k = __float_as_uint(t.f.w);
+    p.C = 0u - (0x4B400000u << p.k);
+    return p;
+}
+
 template <bool PDOT>
-__device__ __forceinline__ int fold_fixed(uint4 pt, uint4 tr, unsigned int n_phase) {
+__device__ __forceinline__ unsigned int fold_fixed_phase(uint4 pt, const FixedPrep &t) {
     const int T1 = (int)pt.x;
-    const unsigned int T0 = pt.y;
-    const unsigned int F1 = tr.x;
-    const int F0 = (int)tr.y;
-    unsigned int acc = (unsigned int)T1 * F1;
-    acc += (unsigned int)__mulhi(T1, F0);
-    acc += __umulhi(T0, F1);
+    unsigned int acc = mad_lo_u32((unsigned int)T1, t.F1, t.C);
+    acc = mad_hi_s32(T1, t.F0, acc);
+    float zin = t.K;
     if (PDOT) {
         const unsigned int U1 = pt.z;
-        const int U0 = (int)pt.w;
-        const int A1 = (int)tr.z;
-        const unsigned int A0 = tr.w;
-        acc += U1 * (unsigned int)A1;
-        acc += (unsigned int)__mulhi(A1, U0);
-        acc += __umulhi(A0, U1);
+        acc = mad_lo_u32(U1, t.A1, acc);
+        acc = mad_hi_u32(t.A0, U1, acc);
+        zin = __fmaf_rn(__uint_as_float(pt.w), t.G2, zin);
     }
-    return (int)__umulhi(acc, n_phase);
+    const float z = __fmaf_rn(__uint_as_float(pt.y), t.G0, zin);
+    return acc + (__float_as_uint(z) << t.k);
+}
+
+template <bool PDOT>
+__device__ __forceinline__ int fold_fixed(uint4 pt, const FixedPrep &t, unsigned int n_phase) {
+    return (int)__umulhi(fold_fixed_phase<PDOT>(pt, t), n_phase);
 }
 
 // ------------------------------------------------------------------ entropy

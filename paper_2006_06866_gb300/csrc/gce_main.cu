@@ -66,47 +66,72 @@ __device__ __forceinline__ FoldConst fold_const(int n_phase) {
     return k;
 }
 
-// Fold<MODE>::slot returns the counter slot of a point for a trial: the phase
-// bin (FP64, FIXED32) or the bin plus 0 or n_phase (SPLIT32, two slots per bin).
+// Fold<MODE> turns a trial's stored constants into the registers its fold
+// needs (prepare) and folds one point into a raw counter slot: the phase bin
+// (FP64, FIXED32) or, for SPLIT32, the bit pattern of the rounding FMA, whose
+// offset kSlotBias is removed once from the counter base address instead of
+// per point.  raw - kSlotBias is the bin, or for SPLIT32 the bin or the bin
+// plus n_phase (two slots per bin).
 template <int MODE> struct Fold;
 template <> struct Fold<GCE_PHASE_FP64> {
+    typedef double2 prep_t;
+    static constexpr int kSlotBias = 0;
+    __device__ __forceinline__ static prep_t prepare(double2 t) { return t; }
     template <bool PDOT>
-    __device__ __forceinline__ static int slot(double p, double2 t, const FoldConst &k) {
+    __device__ __forceinline__ static int raw_slot(double p, const prep_t &t, const FoldConst &k) {
         return fold_fp64<PDOT>(p, t.x, t.y, k.nphi_d, k.n_phase);
     }
     __device__ __forceinline__ static bool has_pdot(double2 t) { return t.y != 0.0; }
 };
 template <> struct Fold<GCE_PHASE_SPLIT32> {
+    typedef float4 prep_t;
+    static constexpr int kSlotBias = 0x4B400000;  // bits of 1.5 2^23
+    __device__ __forceinline__ static prep_t prepare(float4 t) { return t; }
     template <bool PDOT>
-    __device__ __forceinline__ static int slot(float4 p, float4 t, const FoldConst &k) {
-        return fold_split<PDOT>(p, t, k.nphi_f, k.zoff);
+    __device__ __forceinline__ static int raw_slot(float4 p, const prep_t &t, const FoldConst &k) {
+        return fold_split<PDOT>(p, t, k.nphi_f, k.zoff) + kSlotBias;
     }
     __device__ __forceinline__ static bool has_pdot(float4 t) {
         return t.z != 0.0f || t.w != 0.0f;
     }
 };
 template <> struct Fold<GCE_PHASE_FIXED32> {
+    typedef FixedPrep prep_t;
+    static constexpr int kSlotBias = 0;
+    __device__ __forceinline__ static prep_t prepare(const FixedTrial &t) { return fixed_prep(t); }
     template <bool PDOT>
-    __device__ __forceinline__ static int slot(uint4 p, uint4 t, const FoldConst &k) {
+    __device__ __forceinline__ static int raw_slot(uint4 p, const prep_t &t, const FoldConst &k) {
         return fold_fixed<PDOT>(p, t, (unsigned int)k.n_phase);
     }
-    __device__ __forceinline__ static bool has_pdot(uint4 t) { return (t.z | t.w) != 0u; }
+    __device__ __forceinline__ static bool has_pdot(const FixedTrial &t) {
+        return (t.i.z | t.i.w) != 0u;
+    }
 };
+
+// The increment carries no memory clobber, so the compiler may schedule the
+// next points' shared loads around it; compiler_fence() before and after each
+// hot loop keeps the counters' plain loads and stores on their side of it.
+__device__ __forceinline__ void red_shared_inc(unsigned int addr) {
+    asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(addr));
+}
+__device__ __forceinline__ void compiler_fence() { asm volatile("" ::: "memory"); }
 
 // The hot loop: every point of [ka, kb) (shared memory, broadcast) folded for
 // the thread's TPT trials and counted into the thread's private counters.
+// base[s]: shared-memory address of trial s's slot 0 minus the mode's slot bias
+// (mod 2^32); a slot's word is base + (raw << sh), sh = log2(4 * block).
 template <int MODE, int TPT, bool PDOT>
 __device__ __forceinline__ void count_points(
     const typename ModeTraits<MODE>::point_t *__restrict__ pts, int ka, int kb,
-    const typename ModeTraits<MODE>::trial_t (&tc)[TPT], unsigned int *cnt, int stride_j,
-    int stride_s, const FoldConst &fk) {
+    const typename Fold<MODE>::prep_t (&tc)[TPT], const unsigned int (&base)[TPT], int sh,
+    const FoldConst &fk) {
 #pragma unroll 4
     for (int k = ka; k < kb; ++k) {
         const typename ModeTraits<MODE>::point_t p = pts[k];
 #pragma unroll
         for (int s = 0; s < TPT; ++s) {
-            const int j = Fold<MODE>::template slot<PDOT>(p, tc[s], fk);
-            atomicAdd(cnt + s * stride_s + j * stride_j, 1u);
+            const int j = Fold<MODE>::template raw_slot<PDOT>(p, tc[s], fk);
+            red_shared_inc(base[s] + ((unsigned int)j << sh));
         }
     }
 }
@@ -148,6 +173,12 @@ __global__ void __launch_bounds__(512, 2) k_main(MainArgs a) {
     const trial_t *g_tr = reinterpret_cast<const trial_t *>(a.trialc);
     const FoldConst fk = fold_const(n_phase);
     unsigned int *my_cnt = s_cnt + tid;
+    const int sh = 2 + (31 - __clz(B));  // log2(4 * block)
+    unsigned int base[TPT];
+#pragma unroll
+    for (int s = 0; s < TPT; ++s)
+        base[s] = (unsigned int)__cvta_generic_to_shared(my_cnt + s * stride_s) -
+                  ((unsigned int)Fold<MODE>::kSlotBias << sh);
 
     int staged_curve = -1, staged_lo = -1;
     long long item = 0, item_end = 0;
@@ -172,18 +203,18 @@ __global__ void __launch_bounds__(512, 2) k_main(MainArgs a) {
             staged_lo = -1;
         }
 
-        trial_t tc[TPT];
+        typename Fold<MODE>::prep_t tc[TPT];
         long long tt[TPT];
         bool any_pdot = false;
 #pragma unroll
         for (int s = 0; s < TPT; ++s) {
             tt[s] = (long long)tile * (B * TPT) + (long long)s * B + tid;
+            trial_t tr{};
             if (tt[s] < a.n_trials) {
-                tc[s] = g_tr[tt[s]];
-                any_pdot |= Fold<MODE>::has_pdot(tc[s]);
-            } else {
-                tc[s] = trial_t{};
+                tr = g_tr[tt[s]];
+                any_pdot |= Fold<MODE>::has_pdot(tr);
             }
+            tc[s] = Fold<MODE>::prepare(tr);
         }
         const bool pdot = __syncthreads_or(any_pdot) != 0;
 
@@ -205,12 +236,12 @@ __global__ void __launch_bounds__(512, 2) k_main(MainArgs a) {
                 const int s0 = s_seg[i], s1 = s_seg[i + 1];
                 const int ka = max(s0, lo), kb = min(s1, hi);
                 if (ka < kb) {
+                    compiler_fence();
                     if (pdot)
-                        count_points<MODE, TPT, true>(s_pts, ka - lo, kb - lo, tc, my_cnt,
-                                                      stride_j, stride_s, fk);
+                        count_points<MODE, TPT, true>(s_pts, ka - lo, kb - lo, tc, base, sh, fk);
                     else
-                        count_points<MODE, TPT, false>(s_pts, ka - lo, kb - lo, tc, my_cnt,
-                                                       stride_j, stride_s, fk);
+                        count_points<MODE, TPT, false>(s_pts, ka - lo, kb - lo, tc, base, sh, fk);
+                    compiler_fence();
                 }
                 if (s1 > s0 && s1 > lo && s1 <= hi) {
                     // end of magnitude segment i: c_ij = counter - snapshot
@@ -361,16 +392,18 @@ __global__ void k_counts(MainArgs a, long long n_cells, const long long *cell_cu
     const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= n_cells) return;
     const long long c = cell_curve[cell], t = cell_trial[cell];
-    const trial_t tr = reinterpret_cast<const trial_t *>(a.trialc)[t];
+    const trial_t tr0 = reinterpret_cast<const trial_t *>(a.trialc)[t];
+    const typename Fold<MODE>::prep_t tr = Fold<MODE>::prepare(tr0);
     const point_t *pts = reinterpret_cast<const point_t *>(a.payload) + a.offsets[c];
     const int *seg = a.seg + c * (a.n_mag + 1);
     unsigned int *out = counts + cell * a.n_mag * a.n_phase;
-    const bool pdot = Fold<MODE>::has_pdot(tr);
+    const bool pdot = Fold<MODE>::has_pdot(tr0);
     const FoldConst fk = fold_const(a.n_phase);
     for (int i = 0; i < a.n_mag; ++i) {
         for (int k = seg[i]; k < seg[i + 1]; ++k) {
-            int j = pdot ? Fold<MODE>::template slot<true>(pts[k], tr, fk)
-                         : Fold<MODE>::template slot<false>(pts[k], tr, fk);
+            int j = (pdot ? Fold<MODE>::template raw_slot<true>(pts[k], tr, fk)
+                          : Fold<MODE>::template raw_slot<false>(pts[k], tr, fk)) -
+                    Fold<MODE>::kSlotBias;
             if (j >= a.n_phase) j -= a.n_phase;  // SPLIT32's second slot of a bin
             out[i * a.n_phase + j] += 1u;
         }

@@ -97,8 +97,9 @@ __global__ void k_trials(TrialArgs a) {
                 // |x| < 1 needs |c| + |c2| < 1/2: cycles < 2^21 and Pdot cycles < 2^19
                 bad = tau_max * fmax_ >= 2097152.0 || amax * tau_max * tau_max >= 524288.0;
             } else if (MODE == GCE_PHASE_FIXED32) {
+                // F < 2^63, and the Pdot cross term small enough for its FP32 path
                 bad = ldexp(fmax_, fs.e_tau) >= 536870912.0 ||
-                      ldexp(amax, 2 * fs.e_tau) >= 536870912.0;
+                      ldexp(amax, 2 * fs.e_tau) >= 262144.0;
             }
             if (bad) atomicOr(&a.state->err, ERR_RANGE);
         }
@@ -122,17 +123,23 @@ __global__ void k_trials(TrialArgs a) {
             v.w = __double2float_rn(aa - (double)ah);
         } else {
             // Out-of-range values are flagged above; clamp so the conversions stay defined.
-            double F = fmin(ldexp(f, fs.r), 9.2e18);
-            double A = fmax(fmin(ldexp(aa, fs.v), 9.2e18), -9.2e18);
-            int f1, f0, a1, a0;
+            const double F = fmin(ldexp(f, fs.r), 9.2e18);
+            const double A = fmax(fmin(ldexp(aa, fs.v), 9.2e18), -9.2e18);
+            int f1, f0;
             split_balanced(__double2ll_rn(F), &f1, &f0);
-            long long an = -__double2ll_rn(A);
-            a1 = (int)(an >> 32);
-            a0 = (int)(unsigned int)(an & 0xffffffffll);
-            v.x = (unsigned int)f1;
-            v.y = (unsigned int)f0;
-            v.z = (unsigned int)a1;
-            v.w = (unsigned int)a0;
+            const long long an = -__double2ll_rn(A);
+            const int a1 = (int)(an >> 32);
+            const unsigned int a0 = (unsigned int)(an & 0xffffffffll);
+            // k: the smallest shift with F1 < 2^(22+k)
+            const unsigned int uf1 = (unsigned int)f1;
+            const int bits = 32 - __clz(uf1);
+            const int k = bits > 22 ? bits - 22 : 0;
+            const float g0 = __double2float_rn(ldexp((double)uf1, -23 - k));
+            const float g2 = __double2float_rn(ldexp((double)a1, -23 - k));
+            const double kk = 12582912.0 - 8388608.0 * (double)g0 - 8388608.0 * (double)g2 -
+                              ldexp((double)a1, -1 - k);
+            v.i = make_uint4(uf1, (unsigned int)f0, (unsigned int)a1, a0);
+            v.f = make_float4(g0, g2, __double2float_rn(kk), __uint_as_float((unsigned int)k));
         }
         out[t] = v;
     }
@@ -227,10 +234,11 @@ __global__ void __launch_bounds__(kPrepBlock) k_prep(PrepArgs a) {
             const long long U = (long long)((hi << 2) | (lw >> 62));
             int u1, u0;
             split_balanced(U, &u1, &u0);
+            const unsigned int t0 = (unsigned int)(T & 0xffffffffll);
             v.x = (unsigned int)(int)(T >> 32);
-            v.y = (unsigned int)(T & 0xffffffffll);
+            v.y = 0x4B000000u | (t0 >> 9);                               // 2^23 + (T0 >> 9)
             v.z = (unsigned int)u1;
-            v.w = (unsigned int)u0;
+            v.w = 0x4B000000u | (((unsigned int)u0 ^ 0x80000000u) >> 9);  // 2^23 + ((U0+2^31) >> 9)
         }
         out[pos] = v;
     }
