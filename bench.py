@@ -31,12 +31,18 @@ sys.path.insert(0, ROOT)
 
 METRIC = "folded point-trials/s (N_obs×N_P×N_Ṗ) on 1 GB300; FP64 vs split-FP32 phase"
 UNIT = "point-trials/s"
-# IMAD-class (integer multiply) instructions per point-trial of each fold's hot
-# loop without Pdot: 3 limb products + 1 bin multiply-high (FIXED32);
-# FP32 pipe ops for SPLIT32; FP64 pipe ops for FP64 (mul, floor, sub, mul, cvt).
-OPS_PER_PT = {"fixed32": 4, "split32": 9, "fp64": 5}
+# Algorithmic arithmetic of each fold per point-trial without Pdot, and the pipe
+# that executes it (lanes per clock per SM, from the unit counts of the part):
+#   split32: 6 FP32 operations (rounding FMA, subtract, residual FMA, two cross
+#            FMAs, bin FMA) on the FP32 pipe, 128 lanes/clk/SM;
+#   fixed32: one 32-bit multiply-add (1 slot) and two multiply-highs (2 slots
+#            each: half rate) on the integer-multiply pipe, 64 slots/clk/SM;
+#   fp64:    5 FP64 operations (mul, floor, sub, mul, convert), 2 lanes/clk/SM.
+OPS_PER_PT = {"split32": 6, "fixed32": 5, "fp64": 5}
+PIPE = {"split32": ("FP32 pipe", 128), "fixed32": ("integer-multiply pipe (slots)", 64),
+        "fp64": ("FP64 pipe", 2)}
 SM_COUNT = 152
-LANES_PER_SM = {"fixed32": 64, "split32": 128, "fp64": None}
+SM_MAX_MHZ = 2070.0
 
 
 def parse():
@@ -45,7 +51,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gce", choices=["gce", "reference"])
-    ap.add_argument("--mode", default="fixed32", choices=["fixed32", "split32", "fp64"])
+    ap.add_argument("--mode", default="split32", choices=["split32", "fixed32", "fp64"])
     ap.add_argument("--workload", type=int, default=1, help="synthetic workload index (0..4)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64 / SPLIT32 / one-launch-per-curve comparison legs")
@@ -234,7 +240,13 @@ def main():
         cfg = g.Config(batch.n_phase, batch.n_mag, mode, t0=batch.t0, time_kernel=time_kernel)
         g.gce_ce_topk(h, t_d, m_d, offs, p_d, q_d, cfg, k, out_H, out_I, stream=stream)
 
+    tuned = {}
+
     def timed_steps(mode, warmup, steps, with_kernel=False):
+        if mode not in tuned:  # launch-shape autotuning is part of the untimed warm-up
+            cfg = g.Config(batch.n_phase, batch.n_mag, mode, t0=batch.t0)
+            g.gce_autotune(h, cfg, int(batch.n_obs.max()), batch.periods.size * batch.pdots.size)
+            tuned[mode] = g.gce_get_tuning(h, cfg, int(batch.n_obs.max()))
         with torch.cuda.stream(stream):
             for _ in range(warmup):
                 step(mode)
@@ -302,7 +314,7 @@ def main():
 
     extras = {}
     if rank == 0 and world == 1 and not args.no_extras:
-        for mode, n in (("split32", 2), ("fp64", 1)):
+        for mode, n in (("split32", 2), ("fixed32", 2), ("fp64", 1)):
             if mode == args.mode:
                 continue
             ms_m, _, kern_m = timed_steps(mode, 1, n, with_kernel=True)
@@ -341,13 +353,14 @@ def main():
     if kern_ms:
         ops = OPS_PER_PT[args.mode] * pt_step
         achieved = ops / (kern_ms / 1e3) / 1e9
-        lanes = LANES_PER_SM[args.mode]
-        peak = SM_COUNT * lanes * 2070e6 / 1e9 if lanes else None
+        pipe, lanes = PIPE[args.mode]
+        peak = SM_COUNT * lanes * SM_MAX_MHZ * 1e6 / 1e9
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s",
-                "frac": achieved / peak if peak else None, "traffic": None,
+                "frac": achieved / peak, "traffic": None,
                 "kernel": "k_main", "kernel_ms": kern_ms,
                 "kernel_point_trials_per_s": pt_step / (kern_ms / 1e3),
-                "peak_basis": f"{SM_COUNT} SMs x {lanes} integer-multiply lanes/clk x 2070 MHz",
+                "pipe": pipe,
+                "peak_basis": f"{SM_COUNT} SMs x {lanes} lanes/clk x {SM_MAX_MHZ:.0f} MHz",
                 "ops_per_point_trial": OPS_PER_PT[args.mode]}
 
     if rank == 0:
@@ -362,6 +375,7 @@ def main():
                                    f"x {batch.pdots.size} Pdot, {batch.n_phase}x{batch.n_mag} "
                                    f"bins, top-{k}",
                        "phase_mode": args.mode, "point_trials_per_step": pt_step,
+                       "launch_shape": tuned.get(args.mode),
                        "l2": "256 MB buffer written between timed steps",
                        "parallelism": f"replica per GPU x{world}"},
             "e2e": {"value": pt_step * args.steps * world / e2e_t, "unit": UNIT,

@@ -270,7 +270,9 @@ gce_status make_plan(gce_handle h, const Job &j, Plan &pl) {
     pl.block = t.block;
     pl.tpt = t.tpt;
     pl.chunk = std::min(t.chunk, ((pl.n_max + 31) / 32) * 32);
-    pl.table_smem = std::min(pl.n_max + 1, 2048);
+    // the c ln c table in shared memory covers counts up to the staged chunk
+    // (never fewer than 512); larger counts read it from global memory
+    pl.table_smem = std::min(pl.n_max + 1, std::max(512, pl.chunk));
     const int kk = j.kind == JOB_TOPK ? j.k : 0;
     // shrink the staged chunk, then the table, then trials per thread, then the
     // block, until the CTA fits in shared memory
@@ -659,9 +661,12 @@ extern "C" gce_status gce_autotune(gce_handle h, const gce_config *cfg, int32_t 
     if (!h || !cfg) return GCE_ERR_INVALID;
     const int n_obs = std::max(16, std::min<int>(n_obs_hint, GCE_MAX_CURVE_POINTS));
     const long long n_tr = std::max<long long>(4096, std::min<long long>(n_trials_hint, 1 << 22));
-    int64_t offs[9];
-    const int n_curves = 8;
-    for (int c = 0; c <= n_curves; ++c) offs[c] = (int64_t)c * n_obs;
+    // synthetic job of about 5e9 point-trials so that a candidate fills the GPU
+    const int n_curves = (int)std::max<long long>(
+        16, std::min<long long>(256, 5000000000ll / ((long long)n_obs * n_tr)));
+    std::vector<int64_t> offs_v(n_curves + 1);
+    for (int c = 0; c <= n_curves; ++c) offs_v[c] = (int64_t)c * n_obs;
+    const int64_t *offs = offs_v.data();
     if (gce_check_job(offs, n_curves, (int32_t)n_tr, 1, cfg, 0) != GCE_OK)
         return fail(h, GCE_ERR_INVALID, "autotune: invalid config");
     CUDA_TRY(h, cudaSetDevice(h->device));
@@ -687,11 +692,12 @@ extern "C" gce_status gce_autotune(gce_handle h, const gce_config *cfg, int32_t 
     float best_ms = 1e30f;
     const int blocks[] = {128, 256, 512};
     const int tpts[] = {1, 2};
+    const int chunks[] = {512, 1024, 2048};
     gce_config c2 = *cfg;
     c2.flags |= GCE_FLAG_NO_GRAPH;
     do {
         if (cudaMalloc(&d_t, 8 * np) || cudaMalloc(&d_m, 8 * np) || cudaMalloc(&d_p, 8 * n_tr) ||
-            cudaMalloc(&d_d, 8) || cudaMalloc(&d_out, 4 * np / n_obs * n_tr) ||
+            cudaMalloc(&d_d, 8) || cudaMalloc(&d_out, 4 * (size_t)n_curves * n_tr) ||
             cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) || cudaEventCreate(&e0) ||
             cudaEventCreate(&e1)) {
             result = fail(h, GCE_ERR_NOMEM, "autotune: allocation failed");
@@ -701,33 +707,37 @@ extern "C" gce_status gce_autotune(gce_handle h, const gce_config *cfg, int32_t 
         cudaMemcpy(d_m, m.data(), 8 * np, cudaMemcpyHostToDevice);
         cudaMemcpy(d_p, per.data(), 8 * n_tr, cudaMemcpyHostToDevice);
         cudaMemcpy(d_d, pd.data(), 8, cudaMemcpyHostToDevice);
-        for (int b : blocks) {
-            for (int tp : tpts) {
-                gce_tuning cand = default_tuning(cfg->phase_mode, n_obs);
-                cand.block = b;
-                cand.tpt = tp;
-                Job j{};
-                j.kind = JOB_GRID;
-                j.times = d_t; j.mags = d_m; j.h_offsets = offs; j.n_curves = n_curves;
-                j.periods = d_p; j.n_periods = (int)n_tr; j.pdots = d_d; j.n_pdots = 1;
-                j.cfg = &c2; j.out = d_out; j.force = &cand;
-                gce_status st = run_job(h, j, s);
-                if (st != GCE_OK) continue;  // shape does not fit: skip it
-                cudaEventRecord(e0, s);
-                for (int rep = 0; rep < 3; ++rep) run_job(h, j, s);
-                cudaEventRecord(e1, s);
-                if (cudaEventSynchronize(e1) != cudaSuccess) {
-                    result = fail(h, GCE_ERR_CUDA, "autotune: %s", cudaGetErrorString(cudaGetLastError()));
-                    break;
+        std::vector<gce_tuning> cands;
+        for (int b : blocks)
+            for (int tp : tpts)
+                for (int ch : chunks) {
+                    if (ch > 512 && ch >= 2 * n_obs) continue;  // same plan as a smaller chunk
+                    gce_tuning c = default_tuning(cfg->phase_mode, n_obs);
+                    c.block = b;
+                    c.tpt = tp;
+                    c.chunk = ch;
+                    cands.push_back(c);
                 }
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (ms < best_ms) {
-                    best_ms = ms;
-                    best = cand;
-                }
+        for (const gce_tuning &cand : cands) {
+            Job j{};
+            j.kind = JOB_GRID;
+            j.times = d_t; j.mags = d_m; j.h_offsets = offs; j.n_curves = n_curves;
+            j.periods = d_p; j.n_periods = (int)n_tr; j.pdots = d_d; j.n_pdots = 1;
+            j.cfg = &c2; j.out = d_out; j.force = &cand;
+            if (run_job(h, j, s) != GCE_OK) continue;  // shape does not fit: skip it
+            cudaEventRecord(e0, s);
+            for (int rep = 0; rep < 3; ++rep) run_job(h, j, s);
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                result = fail(h, GCE_ERR_CUDA, "autotune: %s", cudaGetErrorString(cudaGetLastError()));
+                break;
             }
-            if (result != GCE_OK) break;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = cand;
+            }
         }
     } while (0);
     if (s) cudaStreamSynchronize(s);

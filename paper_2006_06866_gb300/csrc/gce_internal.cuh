@@ -116,37 +116,41 @@ __device__ __forceinline__ int fold_fp64(double tau, double f, double a, double 
     return min(j, n_phase - 1);
 }
 
-// Eq. 3 in FP32 double-float.  tau f = th fh + (th fl + tl fh) (+ tl fl, below
-// 2^-48 relative): p = RN(th fh) with its exact error e = fma(th, fh, -p)
-// (Dekker's product via FMA); the integer cycles of p are removed exactly by
-// the 1.5 2^23 rounding constant (|p| < 2^21 cycles, checked per job); the
-// small cross terms join e.  The Pdot term a tau^2 is treated the same way
-// with tau^2 = t2h + t2l and a = ah + al.  x = r + c then lies in (-1, 1), and
-// one round-down FMA against the same constant gives n_phase + floor(x
-// n_phase) in [0, 2 n_phase): the returned slot, where slots j and
-// j + n_phase both stand for phase bin j (so no modulo is needed here).
+// Eq. 3 in FP32 double-float.  tau = th + tl and f = fh + fl (float pairs),
+// tau^2 = t2h + t2l and a = ah + al with the a pair stored negated.  The
+// integer cycles of th fh are removed by an FMA against the rounding constant
+// M = 1.5 2^23: t = fma(th, fh, M) holds rint(th fh) + M (|th fh| < 2^21 cycles,
+// checked per job), and r = fma(th, fh, -(t - M)) is the exact product minus
+// that integer, rounded once (|r| <= 1/2).  The cross terms tl fh and th fl
+// (tl fl is below 2^-48 relative) are added by FMA.  The Pdot term -a tau^2 is
+// reduced the same way and the sum reduced once more.  x then lies in
+// (-1, 1), and one round-down FMA against the same constant gives
+// n_phase + floor(x n_phase) in [0, 2 n_phase): the returned slot, where slots
+// j and j + n_phase both stand for phase bin j (so no modulo is needed here).
+// Phase error about 1e-7 cycles (a few 2^-25 roundings).
 constexpr float kRound = 12582912.0f;  // 1.5 * 2^23
 
 template <bool PDOT>
 __device__ __forceinline__ int fold_split(float4 pt, float4 tr, float nphi, float zoff) {
     const float th = pt.x, tl = pt.y;
     const float fh = tr.x, fl = tr.y;
-    float p = __fmul_rn(th, fh);
-    float e = __fmaf_rn(th, fh, -p);
-    float r = __fsub_rn(p, __fsub_rn(__fadd_rn(p, kRound), kRound));
-    float c = __fmaf_rn(th, fl, __fmaf_rn(tl, fh, e));
+    const float t = __fmaf_rn(th, fh, kRound);
+    float r = __fmaf_rn(th, fh, __fsub_rn(kRound, t));
+    float x;
     if (PDOT) {
         const float t2h = pt.z, t2l = pt.w;
-        const float ah = tr.z, al = tr.w;
-        float q = __fmul_rn(ah, t2h);
-        float e2 = __fmaf_rn(ah, t2h, -q);
-        float r2 = __fsub_rn(q, __fsub_rn(__fadd_rn(q, kRound), kRound));
-        float c2 = __fmaf_rn(al, t2h, __fmaf_rn(ah, t2l, e2));
-        float d = __fsub_rn(r, r2);
-        r = __fsub_rn(d, __fsub_rn(__fadd_rn(d, kRound), kRound));
-        c = __fsub_rn(c, c2);
+        const float nah = tr.z, nal = tr.w;  // -a split
+        const float t2 = __fmaf_rn(nah, t2h, kRound);
+        const float r2 = __fmaf_rn(nah, t2h, __fsub_rn(kRound, t2));
+        float c = __fmaf_rn(tl, fh, r);
+        c = __fmaf_rn(th, fl, c);
+        c = __fmaf_rn(nah, t2l, c);
+        c = __fmaf_rn(nal, t2h, c);
+        const float y = __fadd_rn(c, r2);
+        x = __fsub_rn(y, __fsub_rn(__fadd_rn(y, kRound), kRound));
+    } else {
+        x = __fmaf_rn(th, fl, __fmaf_rn(tl, fh, r));
     }
-    const float x = __fadd_rn(r, c);
     const float z = __fmaf_rd(x, nphi, zoff);  // zoff = 1.5 2^23 + n_phase
     return __float_as_int(z) - __float_as_int(kRound);
 }
@@ -225,6 +229,29 @@ __device__ __forceinline__ unsigned int fold_fixed_phase(uint4 pt, const FixedPr
 template <bool PDOT>
 __device__ __forceinline__ int fold_fixed(uint4 pt, const FixedPrep &t, unsigned int n_phase) {
     return (int)__umulhi(fold_fixed_phase<PDOT>(pt, t), n_phase);
+}
+
+// Same fold, with the shift by k known to be zero (every trial of the tile has
+// F1 < 2^22), returning the bin already scaled to a byte offset: with
+// n_sh = n_phase << sh, hi32(phase n_sh) = floor(phase n_phase 2^sh / 2^32),
+// whose low sh bits are the discarded fraction, so masking them leaves
+// bin << sh.
+template <bool PDOT, bool K0>
+__device__ __forceinline__ unsigned int fold_fixed_offset(uint4 pt, const FixedPrep &t,
+                                                          unsigned int n_sh, unsigned int mask) {
+    const int T1 = (int)pt.x;
+    unsigned int acc = mad_lo_u32((unsigned int)T1, t.F1, t.C);
+    acc = mad_hi_s32(T1, t.F0, acc);
+    float zin = t.K;
+    if (PDOT) {
+        const unsigned int U1 = pt.z;
+        acc = mad_lo_u32(U1, t.A1, acc);
+        acc = mad_hi_u32(t.A0, U1, acc);
+        zin = __fmaf_rn(__uint_as_float(pt.w), t.G2, zin);
+    }
+    const unsigned int zb = __float_as_uint(__fmaf_rn(__uint_as_float(pt.y), t.G0, zin));
+    acc += K0 ? zb : __funnelshift_l(0u, zb, t.k);
+    return __umulhi(acc, n_sh) & mask;
 }
 
 // ------------------------------------------------------------------ entropy

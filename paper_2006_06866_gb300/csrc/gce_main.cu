@@ -42,28 +42,44 @@ __device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v)
     return v;
 }
 
+// c ln c from the fixed-point table: shared memory when every count of the curve
+// is covered there (ALL_SMEM), else shared below table_smem and global above.
+template <bool ALL_SMEM>
 __device__ __forceinline__ unsigned long long tab_lookup(const unsigned long long *s_tab,
                                                          int table_smem,
                                                          const unsigned long long *g_tab,
                                                          int c) {
+    if (ALL_SMEM) return s_tab[c];
     return c < table_smem ? s_tab[c] : __ldg(g_tab + c);
 }
+
 
 // Per-mode constants of the fold, computed once per kernel.
 struct FoldConst {
     double nphi_d;
     float nphi_f;
-    float zoff;     // SPLIT32: 1.5 2^23 + n_phase
+    float zoff;          // SPLIT32: 1.5 2^23 + n_phase
     int n_phase;
+    int sh;              // log2 of the byte stride between a thread's slots
+    unsigned int n_sh;   // FIXED32: n_phase << sh
+    unsigned int mask;   // FIXED32: ~(2^sh - 1)
 };
 
-__device__ __forceinline__ FoldConst fold_const(int n_phase) {
+__device__ __forceinline__ FoldConst fold_const(int n_phase, int sh) {
     FoldConst k;
     k.nphi_d = (double)n_phase;
     k.nphi_f = (float)n_phase;
     k.zoff = kRound + (float)n_phase;
     k.n_phase = n_phase;
+    k.sh = sh;
+    k.n_sh = (unsigned int)n_phase << sh;
+    k.mask = ~((1u << sh) - 1u);
     return k;
+}
+
+// j << s on the integer ALU (a funnel shift), not as a multiply.
+__device__ __forceinline__ unsigned int shl_alu(unsigned int j, int s) {
+    return __funnelshift_l(0u, j, s);
 }
 
 // Fold<MODE> turns a trial's stored constants into the registers its fold
@@ -81,7 +97,13 @@ template <> struct Fold<GCE_PHASE_FP64> {
     __device__ __forceinline__ static int raw_slot(double p, const prep_t &t, const FoldConst &k) {
         return fold_fp64<PDOT>(p, t.x, t.y, k.nphi_d, k.n_phase);
     }
+    template <bool PDOT, bool K0>
+    __device__ __forceinline__ static unsigned int offset(double p, const prep_t &t,
+                                                          const FoldConst &k) {
+        return shl_alu((unsigned int)raw_slot<PDOT>(p, t, k), k.sh);
+    }
     __device__ __forceinline__ static bool has_pdot(double2 t) { return t.y != 0.0; }
+    __device__ __forceinline__ static bool k_zero(const prep_t &) { return true; }
 };
 template <> struct Fold<GCE_PHASE_SPLIT32> {
     typedef float4 prep_t;
@@ -91,9 +113,15 @@ template <> struct Fold<GCE_PHASE_SPLIT32> {
     __device__ __forceinline__ static int raw_slot(float4 p, const prep_t &t, const FoldConst &k) {
         return fold_split<PDOT>(p, t, k.nphi_f, k.zoff) + kSlotBias;
     }
+    template <bool PDOT, bool K0>
+    __device__ __forceinline__ static unsigned int offset(float4 p, const prep_t &t,
+                                                          const FoldConst &k) {
+        return shl_alu((unsigned int)raw_slot<PDOT>(p, t, k), k.sh);
+    }
     __device__ __forceinline__ static bool has_pdot(float4 t) {
         return t.z != 0.0f || t.w != 0.0f;
     }
+    __device__ __forceinline__ static bool k_zero(const prep_t &) { return true; }
 };
 template <> struct Fold<GCE_PHASE_FIXED32> {
     typedef FixedPrep prep_t;
@@ -103,9 +131,15 @@ template <> struct Fold<GCE_PHASE_FIXED32> {
     __device__ __forceinline__ static int raw_slot(uint4 p, const prep_t &t, const FoldConst &k) {
         return fold_fixed<PDOT>(p, t, (unsigned int)k.n_phase);
     }
+    template <bool PDOT, bool K0>
+    __device__ __forceinline__ static unsigned int offset(uint4 p, const prep_t &t,
+                                                          const FoldConst &k) {
+        return fold_fixed_offset<PDOT, K0>(p, t, k.n_sh, k.mask);
+    }
     __device__ __forceinline__ static bool has_pdot(const FixedTrial &t) {
         return (t.i.z | t.i.w) != 0u;
     }
+    __device__ __forceinline__ static bool k_zero(const prep_t &t) { return t.k == 0u; }
 };
 
 // The increment carries no memory clobber, so the compiler may schedule the
@@ -120,29 +154,48 @@ __device__ __forceinline__ void compiler_fence() { asm volatile("" ::: "memory")
 // the thread's TPT trials and counted into the thread's private counters.
 // base[s]: shared-memory address of trial s's slot 0 minus the mode's slot bias
 // (mod 2^32); a slot's word is base + (raw << sh), sh = log2(4 * block).
-template <int MODE, int TPT, bool PDOT>
+template <int MODE, int TPT, bool PDOT, bool K0>
 __device__ __forceinline__ void count_points(
     const typename ModeTraits<MODE>::point_t *__restrict__ pts, int ka, int kb,
-    const typename Fold<MODE>::prep_t (&tc)[TPT], const unsigned int (&base)[TPT], int sh,
+    const typename Fold<MODE>::prep_t (&tc)[TPT], const unsigned int (&base)[TPT],
     const FoldConst &fk) {
 #pragma unroll 4
     for (int k = ka; k < kb; ++k) {
         const typename ModeTraits<MODE>::point_t p = pts[k];
 #pragma unroll
-        for (int s = 0; s < TPT; ++s) {
-            const int j = Fold<MODE>::template raw_slot<PDOT>(p, tc[s], fk);
-            red_shared_inc(base[s] + ((unsigned int)j << sh));
-        }
+        for (int s = 0; s < TPT; ++s)
+            red_shared_inc(base[s] + Fold<MODE>::template offset<PDOT, K0>(p, tc[s], fk));
     }
 }
 
 // c_ij of one phase bin at the end of a magnitude segment (low - snapshot), with
-// the snapshot moved up to the current count.
+// the snapshot moved up to the current count: the new word is cur:cur (a byte
+// permute), and new - old = (cur - prev) << 16.
 __device__ __forceinline__ int take_segment(unsigned int *w) {
     const unsigned int v = *w;
-    const unsigned int cur = v & 0xffffu;
-    *w = cur * 0x10001u;
-    return (int)(cur - (v >> 16));
+    const unsigned int nv = __byte_perm(v, 0u, 0x1010);
+    *w = nv;
+    return (int)((nv - v) >> 16);
+}
+
+// End of magnitude segment: add sum_j T(c_ij) of each of the thread's trials.
+template <int SPB, int TPT, bool ALL_SMEM>
+__device__ __forceinline__ void segment_entropy(unsigned int *my_cnt, int stride_s, int stride_j,
+                                                int n_phase, const unsigned long long *s_tab,
+                                                int table_smem, const unsigned long long *g_tab,
+                                                unsigned long long (&s_ij)[TPT]) {
+#pragma unroll
+    for (int s = 0; s < TPT; ++s) {
+        unsigned int *w = my_cnt + s * stride_s;
+        unsigned long long acc = 0ull;
+#pragma unroll 3
+        for (int j = 0; j < n_phase; ++j) {
+            int cij = take_segment(w + j * stride_j);
+            if (SPB == 2) cij += take_segment(w + (j + n_phase) * stride_j);
+            acc += tab_lookup<ALL_SMEM>(s_tab, table_smem, g_tab, cij);
+        }
+        s_ij[s] += acc;
+    }
 }
 
 template <int MODE, int TPT>
@@ -171,9 +224,9 @@ __global__ void __launch_bounds__(512, 2) k_main(MainArgs a) {
 
     const point_t *g_pts = reinterpret_cast<const point_t *>(a.payload);
     const trial_t *g_tr = reinterpret_cast<const trial_t *>(a.trialc);
-    const FoldConst fk = fold_const(n_phase);
     unsigned int *my_cnt = s_cnt + tid;
     const int sh = 2 + (31 - __clz(B));  // log2(4 * block)
+    const FoldConst fk = fold_const(n_phase, sh);
     unsigned int base[TPT];
 #pragma unroll
     for (int s = 0; s < TPT; ++s)
@@ -196,6 +249,7 @@ __global__ void __launch_bounds__(512, 2) k_main(MainArgs a) {
         const int c = a.order[ci];
         const long long off = a.offsets[c];
         const int n = (int)(a.offsets[c + 1] - off);
+        const bool tab_all = n < a.table_smem;  // every count of this curve is <= n
         if (c != staged_curve) {
             __syncthreads();
             for (int i = tid; i <= n_mag; i += B) s_seg[i] = a.seg[(long long)c * (n_mag + 1) + i];
@@ -205,7 +259,7 @@ __global__ void __launch_bounds__(512, 2) k_main(MainArgs a) {
 
         typename Fold<MODE>::prep_t tc[TPT];
         long long tt[TPT];
-        bool any_pdot = false;
+        bool any_pdot = false, all_k0 = true;
 #pragma unroll
         for (int s = 0; s < TPT; ++s) {
             tt[s] = (long long)tile * (B * TPT) + (long long)s * B + tid;
@@ -215,8 +269,10 @@ __global__ void __launch_bounds__(512, 2) k_main(MainArgs a) {
                 any_pdot |= Fold<MODE>::has_pdot(tr);
             }
             tc[s] = Fold<MODE>::prepare(tr);
+            all_k0 &= Fold<MODE>::k_zero(tc[s]);
         }
         const bool pdot = __syncthreads_or(any_pdot) != 0;
+        const bool k0 = MODE != GCE_PHASE_FIXED32 || __syncthreads_and(all_k0) != 0;
 
         for (int i = 0; i < TPT * n_slots; ++i) my_cnt[i * B] = 0u;
         unsigned long long s_ij[TPT];
@@ -237,25 +293,24 @@ __global__ void __launch_bounds__(512, 2) k_main(MainArgs a) {
                 const int ka = max(s0, lo), kb = min(s1, hi);
                 if (ka < kb) {
                     compiler_fence();
-                    if (pdot)
-                        count_points<MODE, TPT, true>(s_pts, ka - lo, kb - lo, tc, base, sh, fk);
-                    else
-                        count_points<MODE, TPT, false>(s_pts, ka - lo, kb - lo, tc, base, sh, fk);
+                    const typename ModeTraits<MODE>::point_t *pp = s_pts;
+                    if (k0) {
+                        if (pdot) count_points<MODE, TPT, true, true>(pp, ka - lo, kb - lo, tc, base, fk);
+                        else count_points<MODE, TPT, false, true>(pp, ka - lo, kb - lo, tc, base, fk);
+                    } else if (MODE == GCE_PHASE_FIXED32) {
+                        if (pdot) count_points<MODE, TPT, true, false>(pp, ka - lo, kb - lo, tc, base, fk);
+                        else count_points<MODE, TPT, false, false>(pp, ka - lo, kb - lo, tc, base, fk);
+                    }
                     compiler_fence();
                 }
                 if (s1 > s0 && s1 > lo && s1 <= hi) {
                     // end of magnitude segment i: c_ij = counter - snapshot
-#pragma unroll
-                    for (int s = 0; s < TPT; ++s) {
-                        unsigned long long acc = 0ull;
-                        unsigned int *w = my_cnt + s * stride_s;
-                        for (int j = 0; j < n_phase; ++j) {
-                            int cij = take_segment(w + j * stride_j);
-                            if (SPB == 2) cij += take_segment(w + (j + n_phase) * stride_j);
-                            acc += tab_lookup(s_tab, a.table_smem, a.table, cij);
-                        }
-                        s_ij[s] += acc;
-                    }
+                    if (tab_all)
+                        segment_entropy<SPB, TPT, true>(my_cnt, stride_s, stride_j, n_phase, s_tab,
+                                                        a.table_smem, a.table, s_ij);
+                    else
+                        segment_entropy<SPB, TPT, false>(my_cnt, stride_s, stride_j, n_phase,
+                                                         s_tab, a.table_smem, a.table, s_ij);
                 }
             }
         }
@@ -270,7 +325,7 @@ __global__ void __launch_bounds__(512, 2) k_main(MainArgs a) {
             for (int j = 0; j < n_phase; ++j) {
                 int cj = (int)(w[j * stride_j] & 0xffffu);
                 if (SPB == 2) cj += (int)(w[(j + n_phase) * stride_j] & 0xffffu);
-                sj += tab_lookup(s_tab, a.table_smem, a.table, cj);
+                sj += tab_lookup<false>(s_tab, a.table_smem, a.table, cj);
             }
             long long d = (long long)(sj - s_ij[s]);
             if (d < 0) d = 0;
@@ -398,7 +453,7 @@ __global__ void k_counts(MainArgs a, long long n_cells, const long long *cell_cu
     const int *seg = a.seg + c * (a.n_mag + 1);
     unsigned int *out = counts + cell * a.n_mag * a.n_phase;
     const bool pdot = Fold<MODE>::has_pdot(tr0);
-    const FoldConst fk = fold_const(a.n_phase);
+    const FoldConst fk = fold_const(a.n_phase, 0);
     for (int i = 0; i < a.n_mag; ++i) {
         for (int k = seg[i]; k < seg[i + 1]; ++k) {
             int j = (pdot ? Fold<MODE>::template raw_slot<true>(pts[k], tr, fk)

@@ -115,12 +115,13 @@ __global__ void k_trials(TrialArgs a) {
             v.x = f;
             v.y = aa;
         } else if constexpr (MODE == GCE_PHASE_SPLIT32) {
+            // f split, and -a split (the fold adds -a tau^2)
             float fh = __double2float_rn(f);
-            float ah = __double2float_rn(aa);
+            float nah = __double2float_rn(-aa);
             v.x = fh;
             v.y = __double2float_rn(f - (double)fh);
-            v.z = ah;
-            v.w = __double2float_rn(aa - (double)ah);
+            v.z = nah;
+            v.w = __double2float_rn(-aa - (double)nah);
         } else {
             // Out-of-range values are flagged above; clamp so the conversions stay defined.
             const double F = fmin(ldexp(f, fs.r), 9.2e18);
