@@ -58,9 +58,36 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU seconds of the oracle baseline sample")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--ref-seconds", type=float, default=60.0,
+                    help="total oracle seconds of the reference arm (spread over its steps)")
     ap.add_argument("--curves", type=int, default=0,
                     help="use only the first N curves of the workload (profiling runs)")
+    ap.add_argument("--shape", default="",
+                    help="block,tpt,chunk: fixed launch shape instead of autotuning (profiling runs)")
     return ap.parse_args()
+
+
+def profiled_traffic(mode, workload, n_curves):
+    """DRAM bytes per full launch of k_main recorded under profiles/ for the batch
+    workload, or None when the kernel sources changed since that capture (their
+    hash no longer matches) or the run is not that workload."""
+    import hashlib
+    prof = os.path.join(ROOT, "profiles", f"k_main_{mode}_batch_100curves.md")
+    if workload != 1 or n_curves != 1000 or not os.path.exists(prof):
+        return None
+    rec = {}
+    for line in open(prof):
+        if ":" in line and line.split(":")[0] in ("traffic_bytes_full_launch",
+                                                  "kernel_sources_sha256_16"):
+            k, v = line.split(":", 1)
+            rec[k.strip()] = v.strip()
+    h = hashlib.sha256()
+    for f in ("gce_main.cu", "gce_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2006_06866_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    if rec.get("kernel_sources_sha256_16") != h.hexdigest()[:16]:
+        return None
+    return int(rec["traffic_bytes_full_launch"]) if "traffic_bytes_full_launch" in rec else None
 
 
 def dist_env():
@@ -98,8 +125,9 @@ def oracle_rate(batch, seconds, n_threads=0):
     dt = max(time.perf_counter() - t0, 1e-4)
     rate1 = cal.point_trials / dt
     threads = os.cpu_count() or 1
-    want = rate1 * threads * seconds
-    n_curves = int(min(batch.n_curves, max(threads, 1)))
+    want = rate1 * threads * seconds  # point-trials the sample should hold
+    per_curve = n_obs * batch.periods.size * batch.pdots.size
+    n_curves = int(min(batch.n_curves, max(threads, int(np.ceil(want / per_curve)))))
     n_periods = int(min(batch.periods.size, max(64, want / (n_curves * n_obs * batch.pdots.size))))
     stride = max(1, batch.periods.size // n_periods)
     sample = batch.subset(list(range(n_curves)), periods=batch.periods[::stride])
@@ -119,7 +147,7 @@ def run_reference(args, rank, world):
         return
     import synth
     batch = synth.make_config(args.workload)
-    per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    per_step = max(0.5, args.ref_seconds / max(1, args.steps + args.warmup))
     rates = []
     used = 1
     desc = ""
@@ -223,6 +251,18 @@ def main():
     batch = synth.make_config(args.workload)
     if args.curves:
         batch = batch.subset(list(range(min(args.curves, batch.n_curves))))
+    if world > 1:
+        # weak scaling: the global batch is the workload once per rank; each rank
+        # searches its own shard of it (balanced by points), no data-path collective
+        from paper_2006_06866_gb300.sharding import shard_arrays, shard_curves
+        n = batch.n_curves
+        glob = batch.subset(list(range(n)) * world)
+        mine = shard_curves(glob.n_obs, world)[rank]
+        t_s, m_s, o_s = shard_arrays(glob.times, glob.mags, glob.offsets, mine)
+        batch = synth.LightCurveBatch(batch.name, t_s, m_s, o_s, batch.periods, batch.pdots,
+                                      batch.n_phase, batch.n_mag, glob.truth_p0[mine],
+                                      glob.truth_pdot[mine], glob.truth_class[mine], batch.t0,
+                                      batch.topk)
     k = batch.topk or 5
     pt_step = batch.point_trials
     t_d = torch.tensor(batch.times, device=dev)
@@ -245,7 +285,12 @@ def main():
     def timed_steps(mode, warmup, steps, with_kernel=False):
         if mode not in tuned:  # launch-shape autotuning is part of the untimed warm-up
             cfg = g.Config(batch.n_phase, batch.n_mag, mode, t0=batch.t0)
-            g.gce_autotune(h, cfg, int(batch.n_obs.max()), batch.periods.size * batch.pdots.size)
+            if args.shape:
+                b_, t_, c_ = (int(x) for x in args.shape.split(","))
+                g.gce_set_tuning(h, cfg, int(batch.n_obs.max()), block=b_, tpt=t_, chunk=c_)
+            else:
+                g.gce_autotune(h, cfg, int(batch.n_obs.max()),
+                               batch.periods.size * batch.pdots.size)
             tuned[mode] = g.gce_get_tuning(h, cfg, int(batch.n_obs.max()))
         with torch.cuda.stream(stream):
             for _ in range(warmup):
@@ -356,7 +401,8 @@ def main():
         pipe, lanes = PIPE[args.mode]
         peak = SM_COUNT * lanes * SM_MAX_MHZ * 1e6 / 1e9
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak,
+                "traffic": profiled_traffic(args.mode, args.workload, batch.n_curves),
                 "kernel": "k_main", "kernel_ms": kern_ms,
                 "kernel_point_trials_per_s": pt_step / (kern_ms / 1e3),
                 "pipe": pipe,
