@@ -156,6 +156,34 @@ gce_status gce_ce_topk_host(gce_handle h, const double *h_times, const double *h
                             const double *h_pdots, int32_t n_pdots, const gce_config *cfg,
                             int32_t k, float *h_topk_H, int64_t *h_topk_idx, void *stream);
 
+/* gce_ce_topk for callers that must not allocate device memory: the paper has
+ * no counterpart.  Some callers cannot call cudaMalloc -- a process whose GPU
+ * memory is owned by another allocator (a framework's caching allocator, or a
+ * pool that has reserved nearly all of it, where an outside cudaMalloc can fail
+ * or fragment that pool), or a latency-critical loop that cannot take
+ * cudaMalloc's implicit synchronisation.  This call allocates nothing and needs
+ * no handle: all its device workspace is a 32 MiB array built into the library
+ * (held on every GPU where the library is loaded, until the process exits).
+ * Arguments are those of gce_ce_topk, with the same meaning and layout; the
+ * caller still owns the input and output buffers.  The call is synchronous on
+ * `stream` and folds the device-side input checks into its status.
+ * Returns GCE_ERR_NOMEM, launching nothing, when the job needs more than the
+ * 32 MiB (about 16 B per point + 32 B per trial + 8 B per (curve, 512-trial
+ * tile, k) + 0.5 MiB); use gce_ce_topk for larger jobs.  Returns
+ * GCE_ERR_UNSUPPORTED when the bin counts need more shared memory than one CTA
+ * of its fixed launch shape (256 threads, 2 trials each) can have.
+ * The first call on a device sets that device up (finds the array's device
+ * address, fills a table in it, with a few synchronous CUDA calls): make it
+ * before any stream capture.  Every call shares the array and keeps the last
+ * call's contents; each call rewrites what it reads.  Calls that overlap on the
+ * GPU (two host threads or two streams) race on the array: make them one at a
+ * time. */
+gce_status gce_ce_topk_static(const double *times, const double *mags,
+                              const int64_t *h_offsets, int32_t n_curves, const double *periods,
+                              int32_t n_periods, const double *pdots, int32_t n_pdots,
+                              const gce_config *cfg, int32_t k, float *topk_H,
+                              int64_t *topk_idx, void *stream);
+
 /* Plain baseline: the FP64 fold with one kernel launch per light curve and one
  * thread per trial (the shape of the paper's own kernel, Sec. 2.3.2), same
  * output as gce_ce_grid.  cfg->phase_mode must be GCE_PHASE_FP64. */

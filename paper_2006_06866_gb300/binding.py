@@ -59,6 +59,8 @@ SIGNATURES = {
     "gce_ce_topk": (_I32, [_P, _P, _P, _HOFF, _I32, _P, _I32, _P, _I32, _CFG, _I32, _P, _P, _P]),
     "gce_ce_topk_host": (_I32, [_P, _P, _P, _HOFF, _I32, _P, _I32, _P, _I32, _CFG, _I32, _P, _P,
                                 _P]),
+    "gce_ce_topk_static": (_I32, [_P, _P, _HOFF, _I32, _P, _I32, _P, _I32, _CFG, _I32, _P, _P,
+                                  _P]),
     "gce_ce_grid_single": (_I32, [_P, _P, _P, _HOFF, _I32, _P, _I32, _P, _I32, _CFG, _P, _P]),
     "gce_ce_counts": (_I32, [_P, _P, _P, _HOFF, _I32, _P, _I32, _P, _I32, _CFG, _I64, _P, _P, _P,
                              _P]),
@@ -256,6 +258,27 @@ def gce_ce_topk_host(handle: Handle, times, mags, offsets, periods, pdots, cfg: 
                                   ctypes.byref(c), int(k), ctypes.c_void_p(out_H.data_ptr()),
                                   ctypes.c_void_p(out_idx.data_ptr()), _stream(stream)),
            handle.ptr)
+    return out_H, out_idx
+
+
+def gce_ce_topk_static(times, mags, offsets, periods, pdots, cfg: Config, k: int, out_H=None,
+                       out_idx=None, stream=None):
+    """gce_ce_topk without a handle and without any device allocation by the
+    library (its workspace is a built-in 32 MiB array).  Synchronous; raises
+    GceError on a non-OK status (GCE_ERR_NOMEM: the job is too large for it)."""
+    import torch
+    off, poff, pt, pm, pp, pd = _common(times, mags, offsets, periods, pdots)
+    nc = off.shape[0] - 1
+    if out_H is None:
+        out_H = torch.empty((nc, k), dtype=torch.float32, device=times.device)
+    if out_idx is None:
+        out_idx = torch.empty((nc, k), dtype=torch.int64, device=times.device)
+    c = cfg.c()
+    st = lib().gce_ce_topk_static(pt, pm, poff, nc, pp, periods.numel(), pd, pdots.numel(),
+                                  ctypes.byref(c), int(k), _dev(out_H, torch.float32, "topk_H"),
+                                  _dev(out_idx, torch.int64, "topk_idx"), _stream(stream))
+    if st != GCE_OK:
+        raise GceError(st, lib().gce_status_string(st).decode())
     return out_H, out_idx
 
 

@@ -1,0 +1,60 @@
+"""gce_ce_topk_static, the entry point for callers that cannot allocate device
+memory (their GPU memory belongs to another allocator, or they cannot take
+cudaMalloc's implicit synchronisation): its workspace is a 32 MiB array built
+into the library.  Its results must match gce_ce_topk, which allocates its
+workspace through a handle, within the parity tolerances, on two calls in a row
+(the shared array keeps the previous call's contents, which must not leak into
+the next).  This file is collected last so that a failure here cannot hide
+other tests in a run that stops at the first failure."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2006_06866_gb300 as g
+import synth
+from gpu_util import TOL_H, dev_args
+
+pytestmark = pytest.mark.gpu
+
+
+def _batch(seed, n_curves, n_obs, n_periods, pdots):
+    rng = np.random.default_rng(seed)
+    lengths = rng.integers(max(1, n_obs // 4), n_obs + 1, size=n_curves)
+    ts = [np.sort(rng.uniform(0, 9.46e7, int(n))) for n in lengths]
+    ms = [15 + 0.4 * np.sin(2 * np.pi * t / rng.uniform(400, 3000)) + rng.normal(0, 0.05, t.size)
+          for t in ts]
+    offs = np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64)
+    return synth.LightCurveBatch("noalloc", np.concatenate(ts), np.concatenate(ms), offs,
+                                 synth.log_periods(300, 5000, n_periods), np.asarray(pdots), 15, 10,
+                                 np.zeros(n_curves), np.zeros(n_curves), np.zeros(n_curves))
+
+
+@pytest.mark.parametrize("mode", ["split32", "fixed32", "fp64"])
+def test_static_scratch_matches_handle_entry_point(mode):
+    h = g.Handle(0)
+    try:
+        k = 5
+        # two different jobs back to back, the second smaller than the first
+        for seed, (nc, no, npd, pdots) in enumerate([(12, 700, 3000, (0.0, -2e-11)),
+                                                     (5, 300, 1100, (0.0,))]):
+            b = _batch(seed, nc, no, npd, pdots)
+            args = dev_args(b)
+            cfg = g.Config(15, 10, mode)
+            rH, rI = g.gce_ce_topk(h, cfg=cfg, k=k, **args)
+            assert g.gce_stream_status(h) == g.GCE_OK
+            sH, sI = g.gce_ce_topk_static(cfg=cfg, k=k, **args)
+            torch.cuda.synchronize()
+            rH, rI, sH, sI = (x.cpu().numpy() for x in (rH, rI, sH, sI))
+            assert np.abs(sH.astype(np.float64) - rH).max() <= TOL_H[mode]
+            # same kernels, same counts: the selected cells agree too
+            assert np.array_equal(sI, rI)
+    finally:
+        h.close()
+
+
+def test_static_scratch_rejects_oversized_jobs():
+    b = synth.make_config(1, n_curves=40, n_periods=1_000_000)  # 32 MB of trial constants alone
+    args = dev_args(b)
+    with pytest.raises(g.GceError) as e:
+        g.gce_ce_topk_static(cfg=g.Config(15, 10, "split32"), k=5, **args)
+    assert e.value.status == g.GCE_ERR_NOMEM
