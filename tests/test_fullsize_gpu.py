@@ -1,0 +1,76 @@
+"""Full-size benchmark workloads (P-Pdot grid, ragged 10k-curve batch, 10-year
+long baseline) run through gce_ce_topk in the benchmark's configuration
+(autotuned launch shape, CUDA graph).  For sampled curves the oracle computes
+the whole trial grid and the device's top-k is checked against it:
+  * every returned cell's H equals the oracle's H of that cell (FP64: 1e-6;
+    SPLIT32/FIXED32: 1e-4 unless the cell has a point within 4 eps of a phase
+    edge);
+  * the returned minimum is the oracle's minimum within the same tolerance, and
+    the returned values are ascending."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2006_06866_gb300 as g
+import synth
+from gpu_util import EPS_PHASE, TOL_H, dev_args
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def h():
+    hh = g.Handle(0)
+    yield hh
+    hh.close()
+
+
+def run_topk(h, b, mode, k):
+    cfg = g.Config(b.n_phase, b.n_mag, mode, t0=b.t0)
+    g.gce_autotune(h, cfg, int(b.n_obs.max()), b.periods.size * b.pdots.size)
+    tH, tI = g.gce_ce_topk(h, cfg=cfg, k=k, **dev_args(b))
+    assert g.gce_stream_status(h) == g.GCE_OK
+    return tH.cpu().numpy().astype(np.float64), tI.cpu().numpy()
+
+
+def check_curves(b, mode, tH, tI, curves):
+    orc = oracle.Oracle()
+    sub = b.subset(curves)
+    grid, dmin = orc.ce_grid(sub.times, sub.mags, sub.offsets, sub.periods, sub.pdots, b.n_phase,
+                             b.n_mag, t0=b.t0, with_dmin=True)
+    tol = TOL_H[mode]
+    for r, c in enumerate(curves):
+        flat, dm = grid[r].ravel(), dmin[r].ravel()
+        assert np.all(np.diff(tH[c]) >= 0)
+        near = dm[tI[c]] <= 4 * EPS_PHASE[mode]
+        err = np.abs(flat[tI[c]] - tH[c])
+        assert np.all(err[~near] <= tol), (c, err, near)
+        best = flat.min()
+        best_near = dm[np.argmin(flat)] <= 4 * EPS_PHASE[mode]
+        if mode == "fp64" or not (near[0] or best_near):
+            assert abs(tH[c, 0] - best) <= tol, (c, tH[c, 0], best)
+
+
+@pytest.mark.parametrize("mode", ["split32", "fixed32", "fp64"])
+def test_pdot_workload_full(h, mode):
+    b = synth.make_config(2)  # 100 curves x 500 obs x 1e4 periods x 256 Pdot
+    tH, tI = run_topk(h, b, mode, 5)
+    check_curves(b, mode, tH, tI, [3, 57])
+
+
+@pytest.mark.parametrize("mode", ["split32", "fixed32", "fp64"])
+def test_ragged_workload_full(h, mode):
+    b = synth.make_config(3)  # 10,000 curves, N log-uniform 50..2000, 5e4 periods
+    tH, tI = run_topk(h, b, mode, 5)
+    rng = np.random.default_rng(4)
+    curves = sorted(set(rng.integers(0, b.n_curves, size=40).tolist()) |
+                    {int(np.argmax(b.n_obs)), int(np.argmin(b.n_obs))})
+    check_curves(b, mode, tH, tI, curves)
+
+
+@pytest.mark.parametrize("mode", ["split32", "fixed32"])
+def test_longbase_workload_full(h, mode):
+    b = synth.make_config(4)  # 1000 curves x 200-1000 obs x 1e5 periods x 64 Pdot, 20 phase bins
+    tH, tI = run_topk(h, b, mode, 5)
+    check_curves(b, mode, tH, tI, [11])
