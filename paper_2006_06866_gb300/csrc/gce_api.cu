@@ -295,10 +295,10 @@ gce_status make_plan(gce_handle h, const Job &j, Plan &pl) {
     const long long tile = (long long)pl.block * pl.tpt;
     pl.n_tiles = (int)((pl.n_trials + tile - 1) / tile);
     pl.n_items = (long long)j.n_curves * pl.n_tiles;
-    CUDA_TRY(h, main_kernel_attrs(cfg->phase_mode, pl.tpt, pl.smem));
+    CUDA_TRY(h, main_kernel_attrs(cfg->phase_mode, pl.tpt, pl.block, pl.smem));
     int occ = 0;
     CUDA_TRY(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                    &occ, main_kernel_ptr(cfg->phase_mode, pl.tpt), pl.block, pl.smem));
+                    &occ, main_kernel_ptr(cfg->phase_mode, pl.tpt, pl.block), pl.block, pl.smem));
     if (occ < 1) return fail(h, GCE_ERR_UNSUPPORTED, "launch shape does not fit on an SM");
     if (t.ctas_per_sm > 0) occ = std::min(occ, t.ctas_per_sm);
     long long g = (long long)h->n_sm * occ;

@@ -231,14 +231,11 @@ __device__ __forceinline__ int fold_fixed(uint4 pt, const FixedPrep &t, unsigned
     return (int)__umulhi(fold_fixed_phase<PDOT>(pt, t), n_phase);
 }
 
-// Same fold, with the shift by k known to be zero (every trial of the tile has
-// F1 < 2^22), returning the bin already scaled to a byte offset: with
-// n_sh = n_phase << sh, hi32(phase n_sh) = floor(phase n_phase 2^sh / 2^32),
-// whose low sh bits are the discarded fraction, so masking them leaves
-// bin << sh.
+// Same fold, specialised for K0 (the shift by k is zero: every trial of the
+// tile has F1 < 2^22), returning the phase bin.
 template <bool PDOT, bool K0>
-__device__ __forceinline__ unsigned int fold_fixed_offset(uint4 pt, const FixedPrep &t,
-                                                          unsigned int n_sh, unsigned int mask) {
+__device__ __forceinline__ unsigned int fold_fixed_bin(uint4 pt, const FixedPrep &t,
+                                                       unsigned int n_phase) {
     const int T1 = (int)pt.x;
     unsigned int acc = mad_lo_u32((unsigned int)T1, t.F1, t.C);
     acc = mad_hi_s32(T1, t.F0, acc);
@@ -251,7 +248,7 @@ __device__ __forceinline__ unsigned int fold_fixed_offset(uint4 pt, const FixedP
     }
     const unsigned int zb = __float_as_uint(__fmaf_rn(__uint_as_float(pt.y), t.G0, zin));
     acc += K0 ? zb : __funnelshift_l(0u, zb, t.k);
-    return __umulhi(acc, n_sh) & mask;
+    return __umulhi(acc, n_phase);
 }
 
 // ------------------------------------------------------------------ entropy
@@ -322,8 +319,8 @@ cudaError_t launch_table(unsigned long long *table, int n_max, cudaStream_t s);
 size_t main_smem_bytes(int mode, int block, int tpt, int chunk, int n_phase, int n_mag,
                        int table_smem, int k);
 size_t single_smem_bytes(int n_phase, int block);
-cudaError_t main_kernel_attrs(int mode, int tpt, size_t smem);
-const void *main_kernel_ptr(int mode, int tpt);
+cudaError_t main_kernel_attrs(int mode, int tpt, int block, size_t smem);
+const void *main_kernel_ptr(int mode, int tpt, int block);
 cudaError_t launch_main(int mode, int tpt, int block, int grid, size_t smem,
                         const MainArgs &a, cudaStream_t s);
 cudaError_t launch_topk_merge(const unsigned long long *cand, int n_curves, int n_tiles,

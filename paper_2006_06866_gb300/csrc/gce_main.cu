@@ -97,10 +97,10 @@ template <> struct Fold<GCE_PHASE_FP64> {
     __device__ __forceinline__ static int raw_slot(double p, const prep_t &t, const FoldConst &k) {
         return fold_fp64<PDOT>(p, t.x, t.y, k.nphi_d, k.n_phase);
     }
-    template <bool PDOT, bool K0>
+    template <bool PDOT, bool K0, int SH>
     __device__ __forceinline__ static unsigned int offset(double p, const prep_t &t,
                                                           const FoldConst &k) {
-        return shl_alu((unsigned int)raw_slot<PDOT>(p, t, k), k.sh);
+        return (unsigned int)raw_slot<PDOT>(p, t, k) << SH;
     }
     __device__ __forceinline__ static bool has_pdot(double2 t) { return t.y != 0.0; }
     __device__ __forceinline__ static bool k_zero(const prep_t &) { return true; }
@@ -113,10 +113,10 @@ template <> struct Fold<GCE_PHASE_SPLIT32> {
     __device__ __forceinline__ static int raw_slot(float4 p, const prep_t &t, const FoldConst &k) {
         return fold_split<PDOT>(p, t, k.nphi_f, k.zoff) + kSlotBias;
     }
-    template <bool PDOT, bool K0>
+    template <bool PDOT, bool K0, int SH>
     __device__ __forceinline__ static unsigned int offset(float4 p, const prep_t &t,
                                                           const FoldConst &k) {
-        return shl_alu((unsigned int)raw_slot<PDOT>(p, t, k), k.sh);
+        return (unsigned int)raw_slot<PDOT>(p, t, k) << SH;
     }
     __device__ __forceinline__ static bool has_pdot(float4 t) {
         return t.z != 0.0f || t.w != 0.0f;
@@ -131,10 +131,10 @@ template <> struct Fold<GCE_PHASE_FIXED32> {
     __device__ __forceinline__ static int raw_slot(uint4 p, const prep_t &t, const FoldConst &k) {
         return fold_fixed<PDOT>(p, t, (unsigned int)k.n_phase);
     }
-    template <bool PDOT, bool K0>
+    template <bool PDOT, bool K0, int SH>
     __device__ __forceinline__ static unsigned int offset(uint4 p, const prep_t &t,
                                                           const FoldConst &k) {
-        return fold_fixed_offset<PDOT, K0>(p, t, k.n_sh, k.mask);
+        return fold_fixed_bin<PDOT, K0>(p, t, (unsigned int)k.n_phase) << SH;
     }
     __device__ __forceinline__ static bool has_pdot(const FixedTrial &t) {
         return (t.i.z | t.i.w) != 0u;
@@ -154,7 +154,7 @@ __device__ __forceinline__ void compiler_fence() { asm volatile("" ::: "memory")
 // the thread's TPT trials and counted into the thread's private counters.
 // base[s]: shared-memory address of trial s's slot 0 minus the mode's slot bias
 // (mod 2^32); a slot's word is base + (raw << sh), sh = log2(4 * block).
-template <int MODE, int TPT, bool PDOT, bool K0>
+template <int MODE, int TPT, int SH, bool PDOT, bool K0>
 __device__ __forceinline__ void count_points(
     const typename ModeTraits<MODE>::point_t *__restrict__ pts, int ka, int kb,
     const typename Fold<MODE>::prep_t (&tc)[TPT], const unsigned int (&base)[TPT],
@@ -164,7 +164,7 @@ __device__ __forceinline__ void count_points(
         const typename ModeTraits<MODE>::point_t p = pts[k];
 #pragma unroll
         for (int s = 0; s < TPT; ++s)
-            red_shared_inc(base[s] + Fold<MODE>::template offset<PDOT, K0>(p, tc[s], fk));
+            red_shared_inc(base[s] + Fold<MODE>::template offset<PDOT, K0, SH>(p, tc[s], fk));
     }
 }
 
@@ -198,8 +198,8 @@ __device__ __forceinline__ void segment_entropy(unsigned int *my_cnt, int stride
     }
 }
 
-template <int MODE, int TPT>
-__global__ void __launch_bounds__(512, 2) k_main(MainArgs a) {
+template <int MODE, int TPT, int LOG2B>
+__global__ void __launch_bounds__(1 << LOG2B, (LOG2B >= 9 ? 2 : (LOG2B == 8 ? 4 : 8))) k_main(MainArgs a) {
     typedef typename ModeTraits<MODE>::point_t point_t;
     typedef typename ModeTraits<MODE>::trial_t trial_t;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -207,7 +207,9 @@ __global__ void __launch_bounds__(512, 2) k_main(MainArgs a) {
 
     if (a.state->err) return;  // inputs failed the device checks: no work
 
-    const int B = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int B = 1 << LOG2B;
+    constexpr int SH = LOG2B + 2;  // log2 of the byte stride between a thread's slots
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n_phase = a.n_phase, n_mag = a.n_mag;
     constexpr int SPB = slots_per_bin(MODE);
     const int n_slots = SPB * n_phase;
@@ -225,13 +227,12 @@ __global__ void __launch_bounds__(512, 2) k_main(MainArgs a) {
     const point_t *g_pts = reinterpret_cast<const point_t *>(a.payload);
     const trial_t *g_tr = reinterpret_cast<const trial_t *>(a.trialc);
     unsigned int *my_cnt = s_cnt + tid;
-    const int sh = 2 + (31 - __clz(B));  // log2(4 * block)
-    const FoldConst fk = fold_const(n_phase, sh);
+    const FoldConst fk = fold_const(n_phase, SH);
     unsigned int base[TPT];
 #pragma unroll
     for (int s = 0; s < TPT; ++s)
         base[s] = (unsigned int)__cvta_generic_to_shared(my_cnt + s * stride_s) -
-                  ((unsigned int)Fold<MODE>::kSlotBias << sh);
+                  ((unsigned int)Fold<MODE>::kSlotBias << SH);
 
     int staged_curve = -1, staged_lo = -1;
     long long item = 0, item_end = 0;
@@ -295,11 +296,11 @@ __global__ void __launch_bounds__(512, 2) k_main(MainArgs a) {
                     compiler_fence();
                     const typename ModeTraits<MODE>::point_t *pp = s_pts;
                     if (k0) {
-                        if (pdot) count_points<MODE, TPT, true, true>(pp, ka - lo, kb - lo, tc, base, fk);
-                        else count_points<MODE, TPT, false, true>(pp, ka - lo, kb - lo, tc, base, fk);
+                        if (pdot) count_points<MODE, TPT, SH, true, true>(pp, ka - lo, kb - lo, tc, base, fk);
+                        else count_points<MODE, TPT, SH, false, true>(pp, ka - lo, kb - lo, tc, base, fk);
                     } else if (MODE == GCE_PHASE_FIXED32) {
-                        if (pdot) count_points<MODE, TPT, true, false>(pp, ka - lo, kb - lo, tc, base, fk);
-                        else count_points<MODE, TPT, false, false>(pp, ka - lo, kb - lo, tc, base, fk);
+                        if (pdot) count_points<MODE, TPT, SH, true, false>(pp, ka - lo, kb - lo, tc, base, fk);
+                        else count_points<MODE, TPT, SH, false, false>(pp, ka - lo, kb - lo, tc, base, fk);
                     }
                     compiler_fence();
                 }
@@ -465,10 +466,33 @@ __global__ void k_counts(MainArgs a, long long n_cells, const long long *cell_cu
     }
 }
 
-template <int MODE, int TPT>
-cudaError_t launch_main_t(int block, int grid, size_t smem, const MainArgs &a, cudaStream_t s) {
-    k_main<MODE, TPT><<<grid, block, smem, s>>>(a);
+template <int MODE, int TPT, int LOG2B>
+cudaError_t launch_main_t(int grid, size_t smem, const MainArgs &a, cudaStream_t s) {
+    k_main<MODE, TPT, LOG2B><<<grid, 1 << LOG2B, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+// The kernel instantiations: mode x trials per thread x block size.
+template <int MODE, int TPT>
+const void *kernel_for_block(int block) {
+    switch (block) {
+        case 64: return (const void *)k_main<MODE, TPT, 6>;
+        case 128: return (const void *)k_main<MODE, TPT, 7>;
+        case 256: return (const void *)k_main<MODE, TPT, 8>;
+        case 512: return (const void *)k_main<MODE, TPT, 9>;
+        default: return nullptr;
+    }
+}
+
+template <int MODE, int TPT>
+cudaError_t launch_for_block(int block, int grid, size_t smem, const MainArgs &a, cudaStream_t s) {
+    switch (block) {
+        case 64: return launch_main_t<MODE, TPT, 6>(grid, smem, a, s);
+        case 128: return launch_main_t<MODE, TPT, 7>(grid, smem, a, s);
+        case 256: return launch_main_t<MODE, TPT, 8>(grid, smem, a, s);
+        case 512: return launch_main_t<MODE, TPT, 9>(grid, smem, a, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace
@@ -484,20 +508,20 @@ size_t main_smem_bytes(int mode, int block, int tpt, int chunk, int n_phase, int
 
 size_t single_smem_bytes(int n_phase, int block) { return 4 * (size_t)n_phase * block; }
 
-const void *main_kernel_ptr(int mode, int tpt) {
+const void *main_kernel_ptr(int mode, int tpt, int block) {
     switch (mode * 4 + tpt) {
-        case GCE_PHASE_FP64 * 4 + 1: return (const void *)k_main<GCE_PHASE_FP64, 1>;
-        case GCE_PHASE_FP64 * 4 + 2: return (const void *)k_main<GCE_PHASE_FP64, 2>;
-        case GCE_PHASE_SPLIT32 * 4 + 1: return (const void *)k_main<GCE_PHASE_SPLIT32, 1>;
-        case GCE_PHASE_SPLIT32 * 4 + 2: return (const void *)k_main<GCE_PHASE_SPLIT32, 2>;
-        case GCE_PHASE_FIXED32 * 4 + 1: return (const void *)k_main<GCE_PHASE_FIXED32, 1>;
-        case GCE_PHASE_FIXED32 * 4 + 2: return (const void *)k_main<GCE_PHASE_FIXED32, 2>;
+        case GCE_PHASE_FP64 * 4 + 1: return kernel_for_block<GCE_PHASE_FP64, 1>(block);
+        case GCE_PHASE_FP64 * 4 + 2: return kernel_for_block<GCE_PHASE_FP64, 2>(block);
+        case GCE_PHASE_SPLIT32 * 4 + 1: return kernel_for_block<GCE_PHASE_SPLIT32, 1>(block);
+        case GCE_PHASE_SPLIT32 * 4 + 2: return kernel_for_block<GCE_PHASE_SPLIT32, 2>(block);
+        case GCE_PHASE_FIXED32 * 4 + 1: return kernel_for_block<GCE_PHASE_FIXED32, 1>(block);
+        case GCE_PHASE_FIXED32 * 4 + 2: return kernel_for_block<GCE_PHASE_FIXED32, 2>(block);
         default: return nullptr;
     }
 }
 
-cudaError_t main_kernel_attrs(int mode, int tpt, size_t smem) {
-    const void *f = main_kernel_ptr(mode, tpt);
+cudaError_t main_kernel_attrs(int mode, int tpt, int block, size_t smem) {
+    const void *f = main_kernel_ptr(mode, tpt, block);
     if (!f) return cudaErrorInvalidValue;
     return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
@@ -505,12 +529,12 @@ cudaError_t main_kernel_attrs(int mode, int tpt, size_t smem) {
 cudaError_t launch_main(int mode, int tpt, int block, int grid, size_t smem, const MainArgs &a,
                         cudaStream_t s) {
     switch (mode * 4 + tpt) {
-        case GCE_PHASE_FP64 * 4 + 1: return launch_main_t<GCE_PHASE_FP64, 1>(block, grid, smem, a, s);
-        case GCE_PHASE_FP64 * 4 + 2: return launch_main_t<GCE_PHASE_FP64, 2>(block, grid, smem, a, s);
-        case GCE_PHASE_SPLIT32 * 4 + 1: return launch_main_t<GCE_PHASE_SPLIT32, 1>(block, grid, smem, a, s);
-        case GCE_PHASE_SPLIT32 * 4 + 2: return launch_main_t<GCE_PHASE_SPLIT32, 2>(block, grid, smem, a, s);
-        case GCE_PHASE_FIXED32 * 4 + 1: return launch_main_t<GCE_PHASE_FIXED32, 1>(block, grid, smem, a, s);
-        case GCE_PHASE_FIXED32 * 4 + 2: return launch_main_t<GCE_PHASE_FIXED32, 2>(block, grid, smem, a, s);
+        case GCE_PHASE_FP64 * 4 + 1: return launch_for_block<GCE_PHASE_FP64, 1>(block, grid, smem, a, s);
+        case GCE_PHASE_FP64 * 4 + 2: return launch_for_block<GCE_PHASE_FP64, 2>(block, grid, smem, a, s);
+        case GCE_PHASE_SPLIT32 * 4 + 1: return launch_for_block<GCE_PHASE_SPLIT32, 1>(block, grid, smem, a, s);
+        case GCE_PHASE_SPLIT32 * 4 + 2: return launch_for_block<GCE_PHASE_SPLIT32, 2>(block, grid, smem, a, s);
+        case GCE_PHASE_FIXED32 * 4 + 1: return launch_for_block<GCE_PHASE_FIXED32, 1>(block, grid, smem, a, s);
+        case GCE_PHASE_FIXED32 * 4 + 2: return launch_for_block<GCE_PHASE_FIXED32, 2>(block, grid, smem, a, s);
         default: return cudaErrorInvalidValue;
     }
 }

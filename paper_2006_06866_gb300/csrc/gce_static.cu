@@ -153,10 +153,10 @@ extern "C" gce_status gce_ce_topk_static(const double *times, const double *mags
     if (L.end > kScratchBytes)
         return fail(GCE_ERR_NOMEM, "job needs more than the 32 MiB of built-in scratch");
 
-    e = main_kernel_attrs(mode, tpt, smem);
+    e = main_kernel_attrs(mode, tpt, block, smem);
     if (e != cudaSuccess) return fail(GCE_ERR_CUDA, cudaGetErrorString(e));
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, main_kernel_ptr(mode, tpt), block, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, main_kernel_ptr(mode, tpt, block), block, smem);
     if (e != cudaSuccess || occ < 1) return fail(GCE_ERR_CUDA, "occupancy query failed");
     const long long n_items = (long long)n_curves * n_tiles;
     long long grid = (long long)d->n_sm * occ;
