@@ -358,31 +358,42 @@ def main():
     d2h = (4 + 8) * batch.n_curves * k
 
     extras = {}
+    # rough rates (point-trials/s) used only to skip comparison legs longer than a minute
+    est_rate = {"split32": 1e12, "fixed32": 8e11, "fp64": 1e11}
     if rank == 0 and world == 1 and not args.no_extras:
         for mode, n in (("split32", 2), ("fixed32", 2), ("fp64", 1)):
             if mode == args.mode:
+                continue
+            if pt_step * n / est_rate[mode] > 60.0:
+                extras[mode] = {"skipped": "one step would take more than a minute"}
                 continue
             ms_m, _, kern_m = timed_steps(mode, 1, n, with_kernel=True)
             extras[mode] = {"value": pt_step * n / (ms_m / 1e3), "ms_per_step": ms_m / n,
                             "kernel_ms": float(np.mean(kern_m))}
         # the plain FP64 one-launch-per-curve kernel (speedup denominator)
-        cfg64 = g.Config(batch.n_phase, batch.n_mag, "fp64", t0=batch.t0, time_kernel=True)
-        with torch.cuda.stream(stream):
-            out = torch.empty((batch.n_curves, batch.pdots.size, batch.periods.size),
-                              dtype=torch.float32, device=dev)
-            g.gce_ce_grid_single(h, t_d, m_d, offs, p_d, q_d, cfg64, out=out, stream=stream)
-            stream.synchronize()
-            flush.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            g.gce_ce_grid_single(h, t_d, m_d, offs, p_d, q_d, cfg64, out=out, stream=stream)
-            e1.record(stream)
-            stream.synchronize()
-            del out
-        ms_single = e0.elapsed_time(e1)
-        extras["fp64_single_launch"] = {"value": pt_step / (ms_single / 1e3),
-                                        "ms_per_step": ms_single}
-        extras["speedup_vs_fp64_single_launch"] = value / world / extras["fp64_single_launch"]["value"]
+        grid_bytes = 4 * batch.n_curves * batch.pdots.size * batch.periods.size
+        if pt_step / 6e10 > 60.0 or grid_bytes > 8e9:
+            extras["fp64_single_launch"] = {"skipped": "one step would take more than a minute"}
+        else:
+            cfg64 = g.Config(batch.n_phase, batch.n_mag, "fp64", t0=batch.t0, time_kernel=True)
+            with torch.cuda.stream(stream):
+                out = torch.empty((batch.n_curves, batch.pdots.size, batch.periods.size),
+                                  dtype=torch.float32, device=dev)
+                g.gce_ce_grid_single(h, t_d, m_d, offs, p_d, q_d, cfg64, out=out, stream=stream)
+                stream.synchronize()
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                g.gce_ce_grid_single(h, t_d, m_d, offs, p_d, q_d, cfg64, out=out, stream=stream)
+                e1.record(stream)
+                stream.synchronize()
+                del out
+            ms_single = e0.elapsed_time(e1)
+            extras["fp64_single_launch"] = {"value": pt_step / (ms_single / 1e3),
+                                            "ms_per_step": ms_single}
+            extras["speedup_vs_fp64_single_launch"] = (
+                value / world / extras["fp64_single_launch"]["value"])
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

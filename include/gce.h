@@ -80,6 +80,10 @@ typedef enum {
 /* flags */
 #define GCE_FLAG_NO_GRAPH 1u      /* launch kernels directly instead of through a CUDA graph */
 #define GCE_FLAG_TIME_KERNEL 2u   /* record CUDA events around the CE kernel (gce_kernel_time) */
+/* 50 %-overlapping phase bins (Sec. 2.3): phase bin j spans [j, j + 2) / n_phase
+ * (modulo 1), so every point counts in its bin and the one below it, and the
+ * probabilities of Eq. 4 are counts over 2N.  Needs n_phase_bins >= 2. */
+#define GCE_FLAG_OVERLAP 4u
 
 typedef struct {
     int32_t n_phase_bins;  /* 1 .. GCE_MAX_PHASE_BINS (the paper uses 15 and 50) */
@@ -144,6 +148,19 @@ gce_status gce_ce_topk(gce_handle h, const double *times, const double *mags,
                        int32_t n_periods, const double *pdots, int32_t n_pdots,
                        const gce_config *cfg, int32_t k, float *topk_H, int64_t *topk_idx,
                        void *stream);
+
+/* gce_ce_topk plus the significance of the minimum (Eq. 5, Sec. 2.3):
+ * rho[c] = (mean[c] - topk_H[c*k]) / std[c], where mean and std (population,
+ * ddof 0) are over all n_pdots * n_periods CE values of curve c.  The moments
+ * are accumulated per trial tile and merged in a fixed order with Chan et al.'s
+ * pairwise update (the batch-statistics merge of Sec. 4), so results are
+ * deterministic.  mean, std: device double[n_curves]; rho: device
+ * float[n_curves] (0 when std is 0). */
+gce_status gce_ce_detect(gce_handle h, const double *times, const double *mags,
+                         const int64_t *h_offsets, int32_t n_curves, const double *periods,
+                         int32_t n_periods, const double *pdots, int32_t n_pdots,
+                         const gce_config *cfg, int32_t k, float *topk_H, int64_t *topk_idx,
+                         double *mean, double *std, float *rho, void *stream);
 
 /* gce_ce_topk on HOST arrays (h_times, h_mags: sum N float64; h_periods,
  * h_pdots; outputs h_topk_H / h_topk_idx of n_curves * k).  Copies inputs to

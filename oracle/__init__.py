@@ -66,15 +66,16 @@ def _bind(lib):
     lib.oracle_entropy.argtypes = [_I64, ctypes.c_int32, ctypes.c_int32]
     lib.oracle_entropy.restype = ctypes.c_double
     lib.oracle_cell.argtypes = [_D, _D, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
-                                ctypes.c_double, ctypes.c_int32, ctypes.c_int32, _I64, _D]
+                                ctypes.c_double, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                _I64, _D]
     lib.oracle_cell.restype = ctypes.c_double
     lib.oracle_ce_grid.argtypes = [_D, _D, _I64, ctypes.c_int32, _D, ctypes.c_int32, _D,
                                    ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
-                                   ctypes.c_double, _D, _D, ctypes.c_int32]
+                                   ctypes.c_double, ctypes.c_int32, _D, _D, ctypes.c_int32]
     lib.oracle_ce_grid.restype = ctypes.c_int
     lib.oracle_ce_cells.argtypes = [_D, _D, _I64, _D, ctypes.c_int32, _D, ctypes.c_int32,
-                                    ctypes.c_int32, ctypes.c_double, ctypes.c_int64, _I64,
-                                    _I64, _D, _D, _I64, ctypes.c_int32]
+                                    ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
+                                    ctypes.c_int64, _I64, _I64, _D, _D, _I64, ctypes.c_int32]
     lib.oracle_ce_cells.restype = ctypes.c_int
     return lib
 
@@ -121,20 +122,20 @@ class Oracle:
         n_mag, n_phase = c.shape
         return self.lib.oracle_entropy(_p(c, _I64), n_mag, n_phase)
 
-    def cell(self, t, m, t0, period, pdot, n_phase, n_mag):
+    def cell(self, t, m, t0, period, pdot, n_phase, n_mag, overlap=False):
         """(H, counts[n_mag, n_phase], dmin) of one curve at one trial."""
         t = np.ascontiguousarray(t, dtype=np.float64)
         m = np.ascontiguousarray(m, dtype=np.float64)
         counts = np.zeros((n_mag, n_phase), dtype=np.int64)
         dmin = ctypes.c_double()
         h = self.lib.oracle_cell(_p(t, _D), _p(m, _D), t.shape[0], float(t0), float(period),
-                                 float(pdot), int(n_phase), int(n_mag), _p(counts, _I64),
-                                 ctypes.byref(dmin))
+                                 float(pdot), int(n_phase), int(n_mag), int(bool(overlap)),
+                                 _p(counts, _I64), ctypes.byref(dmin))
         return h, counts, dmin.value
 
     # --- batches ------------------------------------------------------------
     def ce_grid(self, times, mags, offsets, periods, pdots, n_phase, n_mag, t0=0.0,
-                n_threads=0, with_dmin=False):
+                n_threads=0, with_dmin=False, overlap=False):
         """H[n_curves, n_pdots, n_periods] (float64); with_dmin adds the edge distance."""
         times = np.ascontiguousarray(times, dtype=np.float64)
         mags = np.ascontiguousarray(mags, dtype=np.float64)
@@ -147,12 +148,13 @@ class Oracle:
         used = self.lib.oracle_ce_grid(
             _p(times, _D), _p(mags, _D), _p(offsets, _I64), nc, _p(periods, _D),
             periods.shape[0], _p(pdots, _D), pdots.shape[0], int(n_phase), int(n_mag),
-            float(t0), _p(out, _D), _p(dmin, _D) if with_dmin else None, int(n_threads))
+            float(t0), int(bool(overlap)), _p(out, _D), _p(dmin, _D) if with_dmin else None,
+            int(n_threads))
         self.threads_used = used
         return (out, dmin) if with_dmin else out
 
     def ce_cells(self, times, mags, offsets, periods, pdots, n_phase, n_mag, cell_curve,
-                 cell_trial, t0=0.0, with_counts=False, n_threads=0):
+                 cell_trial, t0=0.0, with_counts=False, n_threads=0, overlap=False):
         """(H[n_cells], dmin[n_cells], counts[n_cells, n_mag, n_phase] or None)."""
         times = np.ascontiguousarray(times, dtype=np.float64)
         mags = np.ascontiguousarray(mags, dtype=np.float64)
@@ -167,10 +169,23 @@ class Oracle:
         counts = np.zeros((n, n_mag, n_phase), dtype=np.int64) if with_counts else None
         used = self.lib.oracle_ce_cells(
             _p(times, _D), _p(mags, _D), _p(offsets, _I64), _p(periods, _D), periods.shape[0],
-            _p(pdots, _D), int(n_phase), int(n_mag), float(t0), n, _p(cc, _I64), _p(ct, _I64),
+            _p(pdots, _D), int(n_phase), int(n_mag), float(t0), int(bool(overlap)), n,
+            _p(cc, _I64), _p(ct, _I64),
             _p(h, _D), _p(dmin, _D), _p(counts, _I64) if with_counts else None, int(n_threads))
         self.threads_used = used
         return h, dmin, counts
+
+
+def oracle_significance(grid):
+    """Eq. 5 per curve from an oracle grid H[c, q, p]: rho = (mu - H_min) / sigma with
+    mu and sigma the mean and population standard deviation (ddof 0; the paper
+    does not say which) of all of the curve's CE values.  Returns (mu, sigma,
+    rho); rho is 0 where sigma is 0."""
+    flat = grid.reshape(grid.shape[0], -1)
+    mu = flat.mean(axis=1)
+    sd = flat.std(axis=1)
+    rho = np.where(sd > 0, (mu - flat.min(axis=1)) / np.where(sd > 0, sd, 1.0), 0.0)
+    return mu, sd, rho
 
 
 def oracle_topk(grid, k):

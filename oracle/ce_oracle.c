@@ -18,7 +18,8 @@
  *     i.e. phi = frac(tau/P - 1/2 Pdot tau^2 / P^2) with tau = t - t0.
  *   - Sec. 2.3: a 2-D histogram with n_mag magnitude bins and n_phase phase bins.
  *   - Eq. 4 (Sec. 2.3): H_c = sum_ij p(m_i,phi_j) ln( p(phi_j) / p(m_i,phi_j) ).
- *   - Sec. 2.3 / Sec. 4: the detection is the grid minimum of H_c.
+ *   - Sec. 2.3 / Sec. 4: the detection is the grid minimum of H_c; its
+ *     significance (Eq. 5) is computed from the grid in oracle/__init__.py.
  *
  * Floating point: IEEE binary64, round-to-nearest, each operation written out
  * in a fixed order (build with -ffp-contract=off, never -ffast-math; the one
@@ -142,10 +143,13 @@ double oracle_entropy(const int64_t *counts, int32_t n_mag, int32_t n_phase)
 /* 2-D histogram of one curve for one (P, Pdot) trial, plus the smallest
  * distance (in cycles) of any folded phase from a phase-bin edge.
  * mag_bins: the curve's magnitude bins (oracle_mag_bins).  counts: n_mag*n_phase,
- * overwritten. */
+ * overwritten.  overlap != 0 reads Sec. 2.3's "each bin has a 50% overlap with
+ * each adjacent bin" as phase bins of width 2/n_phase starting at j/n_phase
+ * (modulo 1): a point in fine bin j then lies in bins j and j - 1 (mod
+ * n_phase), and the probabilities of Eq. 4 are counts over their total 2N. */
 static void cell_counts_from_bins(const double *t, const int32_t *mag_bins, int64_t n,
                                   double t0, double f, double a, int32_t n_phase,
-                                  int32_t n_mag, int64_t *counts, double *dmin)
+                                  int32_t n_mag, int32_t overlap, int64_t *counts, double *dmin)
 {
     memset(counts, 0, sizeof(int64_t) * (size_t)n_mag * (size_t)n_phase);
     double best = 1.0;
@@ -154,6 +158,7 @@ static void cell_counts_from_bins(const double *t, const int32_t *mag_bins, int6
         double y;
         int32_t j = oracle_phase_bin(tau, f, a, n_phase, &y);
         counts[(int64_t)mag_bins[k] * n_phase + j] += 1;
+        if (overlap) counts[(int64_t)mag_bins[k] * n_phase + (j + n_phase - 1) % n_phase] += 1;
         double fr = y - floor(y);
         double d = fr < 1.0 - fr ? fr : 1.0 - fr;
         d /= (double)n_phase;
@@ -165,14 +170,14 @@ static void cell_counts_from_bins(const double *t, const int32_t *mag_bins, int6
 /* Counts, H and edge distance of one curve for one trial.  counts may be NULL. */
 double oracle_cell(const double *t, const double *m, int64_t n, double t0,
                    double period, double pdot, int32_t n_phase, int32_t n_mag,
-                   int64_t *counts_out, double *dmin)
+                   int32_t overlap, int64_t *counts_out, double *dmin)
 {
     int32_t *bins = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
     int64_t *counts = (int64_t *)malloc(sizeof(int64_t) * (size_t)n_mag * (size_t)n_phase);
     double f, a;
     oracle_mag_bins(m, n, n_mag, bins);
     oracle_trial_constants(period, pdot, &f, &a);
-    cell_counts_from_bins(t, bins, n, t0, f, a, n_phase, n_mag, counts, dmin);
+    cell_counts_from_bins(t, bins, n, t0, f, a, n_phase, n_mag, overlap, counts, dmin);
     double h = oracle_entropy(counts, n_mag, n_phase);
     if (counts_out) memcpy(counts_out, counts, sizeof(int64_t) * (size_t)n_mag * (size_t)n_phase);
     free(counts);
@@ -191,7 +196,8 @@ double oracle_cell(const double *t, const double *m, int64_t n, double t0,
 int oracle_ce_grid(const double *times, const double *mags, const int64_t *offsets,
                    int32_t n_curves, const double *periods, int32_t n_periods,
                    const double *pdots, int32_t n_pdots, int32_t n_phase, int32_t n_mag,
-                   double t0, double *out_H, double *out_dmin, int32_t n_threads)
+                   double t0, int32_t overlap, double *out_H, double *out_dmin,
+                   int32_t n_threads)
 {
     int used = 1;
     int64_t rows = (int64_t)n_curves * n_pdots;
@@ -214,7 +220,8 @@ int oracle_ce_grid(const double *times, const double *mags, const int64_t *offse
         for (int32_t p = 0; p < n_periods; ++p) {
             double f, a, dmin;
             oracle_trial_constants(periods[p], pdots[q], &f, &a);
-            cell_counts_from_bins(times + lo, bins, n, t0, f, a, n_phase, n_mag, counts, &dmin);
+            cell_counts_from_bins(times + lo, bins, n, t0, f, a, n_phase, n_mag, overlap, counts,
+                                  &dmin);
             int64_t o = r * n_periods + p;
             out_H[o] = oracle_entropy(counts, n_mag, n_phase);
             if (out_dmin) out_dmin[o] = dmin;
@@ -230,7 +237,7 @@ int oracle_ce_grid(const double *times, const double *mags, const int64_t *offse
  * n_mag*n_phase counts per cell, magnitude-bin major. */
 int oracle_ce_cells(const double *times, const double *mags, const int64_t *offsets,
                     const double *periods, int32_t n_periods, const double *pdots,
-                    int32_t n_phase, int32_t n_mag, double t0, int64_t n_cells,
+                    int32_t n_phase, int32_t n_mag, double t0, int32_t overlap, int64_t n_cells,
                     const int64_t *cell_curve, const int64_t *cell_trial,
                     double *out_H, double *out_dmin, int64_t *out_counts, int32_t n_threads)
 {
@@ -251,7 +258,7 @@ int oracle_ce_cells(const double *times, const double *mags, const int64_t *offs
         int64_t *cnt = out_counts ? out_counts + k * (int64_t)n_mag * n_phase : NULL;
         double dmin;
         out_H[k] = oracle_cell(times + lo, mags + lo, n, t0, periods[p], pdots[q],
-                               n_phase, n_mag, cnt, &dmin);
+                               n_phase, n_mag, overlap, cnt, &dmin);
         if (out_dmin) out_dmin[k] = dmin;
     }
     return used;

@@ -20,6 +20,7 @@ GCE_OK, GCE_ERR_INVALID, GCE_ERR_CUDA, GCE_ERR_NOMEM, GCE_ERR_UNSUPPORTED = rang
 GCE_PHASE_FP64, GCE_PHASE_SPLIT32, GCE_PHASE_FIXED32 = 0, 1, 2
 GCE_FLAG_NO_GRAPH = 1
 GCE_FLAG_TIME_KERNEL = 2
+GCE_FLAG_OVERLAP = 4
 GCE_MAX_PHASE_BINS, GCE_MAX_MAG_BINS, GCE_MAX_CURVE_POINTS, GCE_MAX_TOPK = 256, 255, 65535, 64
 MODES = {"fp64": GCE_PHASE_FP64, "split32": GCE_PHASE_SPLIT32, "fixed32": GCE_PHASE_FIXED32}
 
@@ -57,6 +58,8 @@ SIGNATURES = {
     "gce_check_job": (_I32, [_HOFF, _I32, _I32, _I32, _CFG, _I32]),
     "gce_ce_grid": (_I32, [_P, _P, _P, _HOFF, _I32, _P, _I32, _P, _I32, _CFG, _P, _P]),
     "gce_ce_topk": (_I32, [_P, _P, _P, _HOFF, _I32, _P, _I32, _P, _I32, _CFG, _I32, _P, _P, _P]),
+    "gce_ce_detect": (_I32, [_P, _P, _P, _HOFF, _I32, _P, _I32, _P, _I32, _CFG, _I32, _P, _P, _P,
+                             _P, _P, _P]),
     "gce_ce_topk_host": (_I32, [_P, _P, _P, _HOFF, _I32, _P, _I32, _P, _I32, _CFG, _I32, _P, _P,
                                 _P]),
     "gce_ce_topk_static": (_I32, [_P, _P, _HOFF, _I32, _P, _I32, _P, _I32, _CFG, _I32, _P, _P,
@@ -98,11 +101,13 @@ class Config:
     t0: float = 0.0
     use_graph: bool = True
     time_kernel: bool = False
+    overlap: bool = False
 
     def c(self):
         mode = MODES[self.phase_mode] if isinstance(self.phase_mode, str) else self.phase_mode
         flags = (0 if self.use_graph else GCE_FLAG_NO_GRAPH) | \
-            (GCE_FLAG_TIME_KERNEL if self.time_kernel else 0)
+            (GCE_FLAG_TIME_KERNEL if self.time_kernel else 0) | \
+            (GCE_FLAG_OVERLAP if self.overlap else 0)
         return gce_config(int(self.n_phase_bins), int(self.n_mag_bins), int(mode), flags,
                           float(self.t0))
 
@@ -225,6 +230,28 @@ def gce_ce_topk(handle: Handle, times, mags, offsets, periods, pdots, cfg: Confi
                              _dev(out_idx, torch.int64, "topk_idx"), _stream(stream)),
            handle.ptr)
     return out_H, out_idx
+
+
+def gce_ce_detect(handle: Handle, times, mags, offsets, periods, pdots, cfg: Config, k: int,
+                  stream=None):
+    """(topk_H, topk_idx, mean, std, rho) CUDA tensors: the k smallest cells and the
+    significance rho = (mean - H_min) / std of each curve (Eq. 5)."""
+    import torch
+    off, poff, pt, pm, pp, pd = _common(times, mags, offsets, periods, pdots)
+    nc = off.shape[0] - 1
+    dev = times.device
+    tH = torch.empty((nc, k), dtype=torch.float32, device=dev)
+    tI = torch.empty((nc, k), dtype=torch.int64, device=dev)
+    mean = torch.empty(nc, dtype=torch.float64, device=dev)
+    std = torch.empty(nc, dtype=torch.float64, device=dev)
+    rho = torch.empty(nc, dtype=torch.float32, device=dev)
+    c = cfg.c()
+    _check(lib().gce_ce_detect(handle.ptr, pt, pm, poff, nc, pp, periods.numel(), pd,
+                               pdots.numel(), ctypes.byref(c), int(k),
+                               _dev(tH, torch.float32, "topk_H"), _dev(tI, torch.int64, "topk_idx"),
+                               _dev(mean, torch.float64, "mean"), _dev(std, torch.float64, "std"),
+                               _dev(rho, torch.float32, "rho"), _stream(stream)), handle.ptr)
+    return tH, tI, mean, std, rho
 
 
 def gce_ce_topk_host(handle: Handle, times, mags, offsets, periods, pdots, cfg: Config, k: int,

@@ -49,7 +49,7 @@ struct gce_handle_s {
     int n_sm = 0;
     int smem_optin = 0;
     std::string last_error;
-    DevBuf payload, seg, trialc, order, offsets, cand, table, state, in_times, in_mags,
+    DevBuf payload, seg, trialc, order, offsets, cand, stats, table, state, in_times, in_mags,
         in_periods, in_pdots, out_H, out_idx;
     int table_n = -1;                    // largest count the table covers
     int *h_order = nullptr;              // pinned staging
@@ -169,6 +169,7 @@ extern "C" gce_status gce_check_job(const int64_t *h_offsets, int32_t n_curves,
         cfg->phase_mode != GCE_PHASE_FIXED32)
         return GCE_ERR_INVALID;
     if (!std::isfinite(cfg->t0)) return GCE_ERR_INVALID;
+    if ((cfg->flags & GCE_FLAG_OVERLAP) && cfg->n_phase_bins < 2) return GCE_ERR_INVALID;
     if (n_curves < 0 || n_periods < 1 || n_pdots < 1) return GCE_ERR_INVALID;
     const long long n_trials = (long long)n_periods * n_pdots;
     if (n_trials >= (1ll << 32)) return GCE_ERR_INVALID;
@@ -220,7 +221,7 @@ extern "C" gce_status gce_destroy(gce_handle h) {
     cudaSetDevice(h->device);
     cudaDeviceSynchronize();
     for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
-    DevBuf *bufs[] = {&h->payload, &h->seg, &h->trialc, &h->order, &h->offsets, &h->cand,
+    DevBuf *bufs[] = {&h->payload, &h->seg, &h->trialc, &h->order, &h->offsets, &h->cand, &h->stats,
                       &h->table, &h->state, &h->in_times, &h->in_mags, &h->in_periods,
                       &h->in_pdots, &h->out_H, &h->out_idx};
     for (DevBuf *b : bufs)
@@ -247,6 +248,8 @@ struct Job {
     float *out;                  // grid (JOB_GRID, JOB_SINGLE)
     float *topk_H;               // JOB_TOPK
     int64_t *topk_idx;
+    double *mean, *std_dev;      // JOB_TOPK with significance (rho != nullptr)
+    float *rho;
     long long n_cells;           // JOB_COUNTS
     const int64_t *cell_curve, *cell_trial;
     uint32_t *counts;
@@ -278,7 +281,8 @@ gce_status make_plan(gce_handle h, const Job &j, Plan &pl) {
     // block, until the CTA fits in shared memory
     auto size = [&]() {
         return main_smem_bytes(cfg->phase_mode, pl.block, pl.tpt, pl.chunk, cfg->n_phase_bins,
-                               cfg->n_mag_bins, pl.table_smem, kk);
+                               cfg->n_mag_bins, pl.table_smem, kk,
+                               (cfg->flags & GCE_FLAG_OVERLAP) ? 1 : 0);
     };
     pl.smem = size();
     while (pl.smem > (size_t)h->smem_optin) {
@@ -365,6 +369,8 @@ gce_status enqueue(gce_handle h, const Job &j, const Plan &pl, cudaStream_t s, b
     ma.out = nullptr;
     ma.cand = nullptr;
     ma.k = 0;
+    ma.stats = nullptr;
+    ma.overlap = (cfg->flags & GCE_FLAG_OVERLAP) ? 1 : 0;
     ma.state = st;
     const bool timed = (cfg->flags & GCE_FLAG_TIME_KERNEL) != 0;
     gce_status ms;
@@ -378,11 +384,13 @@ gce_status enqueue(gce_handle h, const Job &j, const Plan &pl, cudaStream_t s, b
         case JOB_TOPK:
             ma.cand = (unsigned long long *)h->cand.p;
             ma.k = j.k;
+            if (j.rho) ma.stats = (TileStats *)h->stats.p;
             if (timed && (ms = mark(h, h->k0, s, capturing)) != GCE_OK) return ms;
             CUDA_TRY(h, launch_main(mode, pl.tpt, pl.block, pl.grid, pl.smem, ma, s));
             if (timed && (ms = mark(h, h->k1, s, capturing)) != GCE_OK) return ms;
             CUDA_TRY(h, launch_topk_merge((const unsigned long long *)h->cand.p, j.n_curves,
-                                          pl.n_tiles, j.k, j.topk_H, (long long *)j.topk_idx, st, s));
+                                          pl.n_tiles, j.k, j.topk_H, (long long *)j.topk_idx,
+                                          ma.stats, j.mean, j.std_dev, j.rho, st, s));
             break;
         case JOB_SINGLE:
             ma.out = j.out;
@@ -416,6 +424,8 @@ gce_status run_job(gce_handle h, const Job &j, cudaStream_t s) {
         return fail(h, GCE_ERR_INVALID, "NULL output array");
     if (j.kind == JOB_TOPK && (!j.topk_H || !j.topk_idx))
         return fail(h, GCE_ERR_INVALID, "NULL output array");
+    if (j.kind == JOB_TOPK && (j.rho || j.mean || j.std_dev) && !(j.rho && j.mean && j.std_dev))
+        return fail(h, GCE_ERR_INVALID, "significance needs all of mean, std and rho");
     if (j.kind == JOB_COUNTS && j.n_cells > 0 && (!j.cell_curve || !j.cell_trial || !j.counts))
         return fail(h, GCE_ERR_INVALID, "NULL cell array");
     CUDA_TRY(h, cudaSetDevice(h->device));
@@ -433,6 +443,9 @@ gce_status run_job(gce_handle h, const Job &j, cudaStream_t s) {
     if ((st = ensure(h, h->offsets, sizeof(long long) * (size_t)(j.n_curves + 1))) != GCE_OK) return st;
     if (j.kind == JOB_TOPK &&
         (st = ensure(h, h->cand, 8 * (size_t)j.n_curves * pl.n_tiles * j.k)) != GCE_OK)
+        return st;
+    if (j.kind == JOB_TOPK && j.rho &&
+        (st = ensure(h, h->stats, sizeof(TileStats) * (size_t)j.n_curves * pl.n_tiles)) != GCE_OK)
         return st;
     if (pl.n_max > h->table_n) {
         if ((st = ensure(h, h->table, 8 * (size_t)(pl.n_max + 1))) != GCE_OK) return st;
@@ -478,7 +491,8 @@ gce_status run_job(gce_handle h, const Job &j, cudaStream_t s) {
             return st;
         }
         if (e != cudaSuccess) return fail(h, GCE_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
-        GraphKey key{j.kind, mode, j.n_curves, j.n_periods, j.n_pdots, j.cfg->n_phase_bins,
+        GraphKey key{j.kind * 4 + (j.rho ? 2 : 0) + ((j.cfg->flags & GCE_FLAG_OVERLAP) ? 1 : 0),
+                     mode, j.n_curves, j.n_periods, j.n_pdots, j.cfg->n_phase_bins,
                      j.cfg->n_mag_bins, j.k, pl.block, pl.tpt, pl.grid, pl.chunk, pl.table_smem,
                      pl.grab, pl.n_points};
         auto it = h->graphs.find(key);
@@ -551,6 +565,22 @@ extern "C" gce_status gce_ce_topk(gce_handle h, const double *times, const doubl
     j.times = times; j.mags = mags; j.h_offsets = h_offsets; j.n_curves = n_curves;
     j.periods = periods; j.n_periods = n_periods; j.pdots = pdots; j.n_pdots = n_pdots;
     j.cfg = cfg; j.k = k; j.topk_H = topk_H; j.topk_idx = topk_idx;
+    return run_job(h, j, (cudaStream_t)stream);
+}
+
+extern "C" gce_status gce_ce_detect(gce_handle h, const double *times, const double *mags,
+                                    const int64_t *h_offsets, int32_t n_curves,
+                                    const double *periods, int32_t n_periods,
+                                    const double *pdots, int32_t n_pdots, const gce_config *cfg,
+                                    int32_t k, float *topk_H, int64_t *topk_idx, double *mean,
+                                    double *std_dev, float *rho, void *stream) {
+    if (!mean || !std_dev || !rho) return h ? fail(h, GCE_ERR_INVALID, "NULL moment output") : GCE_ERR_INVALID;
+    Job j{};
+    j.kind = JOB_TOPK;
+    j.times = times; j.mags = mags; j.h_offsets = h_offsets; j.n_curves = n_curves;
+    j.periods = periods; j.n_periods = n_periods; j.pdots = pdots; j.n_pdots = n_pdots;
+    j.cfg = cfg; j.k = k; j.topk_H = topk_H; j.topk_idx = topk_idx;
+    j.mean = mean; j.std_dev = std_dev; j.rho = rho;
     return run_job(h, j, (cudaStream_t)stream);
 }
 

@@ -287,6 +287,11 @@ struct TrialArgs {
     JobState *state;
 };
 
+// Moments of a tile's H values: count, mean, sum of squared deviations.
+struct TileStats {
+    double n, mean, m2;
+};
+
 struct MainArgs {
     const void *payload;
     const long long *offsets;
@@ -305,6 +310,8 @@ struct MainArgs {
     float *out;                // grid or nullptr
     unsigned long long *cand;  // top-k candidates [n_curves][n_tiles][k] or nullptr
     int k;
+    TileStats *stats;          // per-tile moments [n_curves][n_tiles] or nullptr
+    int overlap;               // 50 %-overlapping phase bins
     JobState *state;
 };
 
@@ -317,14 +324,15 @@ cudaError_t launch_trials(int mode, const TrialArgs &a, cudaStream_t s);
 cudaError_t launch_prep(int mode, const PrepArgs &a, cudaStream_t s);
 cudaError_t launch_table(unsigned long long *table, int n_max, cudaStream_t s);
 size_t main_smem_bytes(int mode, int block, int tpt, int chunk, int n_phase, int n_mag,
-                       int table_smem, int k);
+                       int table_smem, int k, int overlap);
 size_t single_smem_bytes(int n_phase, int block);
 cudaError_t main_kernel_attrs(int mode, int tpt, int block, size_t smem);
 const void *main_kernel_ptr(int mode, int tpt, int block);
 cudaError_t launch_main(int mode, int tpt, int block, int grid, size_t smem,
                         const MainArgs &a, cudaStream_t s);
 cudaError_t launch_topk_merge(const unsigned long long *cand, int n_curves, int n_tiles,
-                              int k, float *topk_H, long long *topk_idx, const JobState *st,
+                              int k, float *topk_H, long long *topk_idx, const TileStats *stats,
+                              double *mean, double *std_dev, float *rho, const JobState *st,
                               cudaStream_t s);
 cudaError_t launch_single(const MainArgs &a, int curve, long long n_points, cudaStream_t s);
 cudaError_t launch_counts(int mode, const MainArgs &a, long long n_cells,

@@ -152,9 +152,11 @@ __device__ __forceinline__ void compiler_fence() { asm volatile("" ::: "memory")
 
 // The hot loop: every point of [ka, kb) (shared memory, broadcast) folded for
 // the thread's TPT trials and counted into the thread's private counters.
-// base[s]: shared-memory address of trial s's slot 0 minus the mode's slot bias
-// (mod 2^32); a slot's word is base + (raw << sh), sh = log2(4 * block).
-template <int MODE, int TPT, int SH, bool PDOT, bool K0>
+// base[s]: shared-memory address of trial s's logical slot 0 minus the mode's
+// slot bias (mod 2^32); a slot's word is base + (raw << SH), SH = log2(4 block).
+// With OVL (50 %-overlapping phase bins, Sec. 2.3) each point also counts in
+// the bin below, the word one slot stride lower (logical slot -1 exists).
+template <int MODE, int TPT, int SH, bool PDOT, bool K0, bool OVL>
 __device__ __forceinline__ void count_points(
     const typename ModeTraits<MODE>::point_t *__restrict__ pts, int ka, int kb,
     const typename Fold<MODE>::prep_t (&tc)[TPT], const unsigned int (&base)[TPT],
@@ -163,9 +165,22 @@ __device__ __forceinline__ void count_points(
     for (int k = ka; k < kb; ++k) {
         const typename ModeTraits<MODE>::point_t p = pts[k];
 #pragma unroll
-        for (int s = 0; s < TPT; ++s)
-            red_shared_inc(base[s] + Fold<MODE>::template offset<PDOT, K0, SH>(p, tc[s], fk));
+        for (int s = 0; s < TPT; ++s) {
+            const unsigned int addr =
+                base[s] + Fold<MODE>::template offset<PDOT, K0, SH>(p, tc[s], fk);
+            red_shared_inc(addr);
+            if (OVL) red_shared_inc(addr - (1u << SH));
+        }
     }
+}
+
+template <int MODE, int TPT, int SH, bool PDOT, bool K0>
+__device__ __forceinline__ void count_points_ovl(
+    bool ovl, const typename ModeTraits<MODE>::point_t *__restrict__ pts, int ka, int kb,
+    const typename Fold<MODE>::prep_t (&tc)[TPT], const unsigned int (&base)[TPT],
+    const FoldConst &fk) {
+    if (ovl) count_points<MODE, TPT, SH, PDOT, K0, true>(pts, ka, kb, tc, base, fk);
+    else count_points<MODE, TPT, SH, PDOT, K0, false>(pts, ka, kb, tc, base, fk);
 }
 
 // c_ij of one phase bin at the end of a magnitude segment (low - snapshot), with
@@ -179,23 +194,65 @@ __device__ __forceinline__ int take_segment(unsigned int *w) {
 }
 
 // End of magnitude segment: add sum_j T(c_ij) of each of the thread's trials.
-template <int SPB, int TPT, bool ALL_SMEM>
+// The counters of trial s start at my_cnt + s stride_s (physical slot 0);
+// logical slot l is physical l + ovl, logical slot -1 (overlap only) belongs to
+// the last bin, and with two slots per bin logical j + n_phase belongs to bin j.
+template <int SPB, int TPT, bool ALL_SMEM, bool OVL>
 __device__ __forceinline__ void segment_entropy(unsigned int *my_cnt, int stride_s, int stride_j,
                                                 int n_phase, const unsigned long long *s_tab,
                                                 int table_smem, const unsigned long long *g_tab,
                                                 unsigned long long (&s_ij)[TPT]) {
 #pragma unroll
     for (int s = 0; s < TPT; ++s) {
-        unsigned int *w = my_cnt + s * stride_s;
+        unsigned int *w = my_cnt + s * stride_s + (OVL ? stride_j : 0);
         unsigned long long acc = 0ull;
+        if (OVL) {  // logical slot -1: the last bin
+            int c_last = take_segment(w - stride_j);
+            c_last += take_segment(w + (n_phase - 1) * stride_j);
+            if (SPB == 2) c_last += take_segment(w + (2 * n_phase - 1) * stride_j);
+            acc += tab_lookup<ALL_SMEM>(s_tab, table_smem, g_tab, c_last);
+        }
+        const int n_j = OVL ? n_phase - 1 : n_phase;
 #pragma unroll 3
-        for (int j = 0; j < n_phase; ++j) {
+        for (int j = 0; j < n_j; ++j) {
             int cij = take_segment(w + j * stride_j);
             if (SPB == 2) cij += take_segment(w + (j + n_phase) * stride_j);
             acc += tab_lookup<ALL_SMEM>(s_tab, table_smem, g_tab, cij);
         }
         s_ij[s] += acc;
     }
+}
+
+template <int SPB, int TPT, bool OVL>
+__device__ __forceinline__ void segment_entropy_any(bool tab_all, unsigned int *my_cnt,
+                                                    int stride_s, int stride_j, int n_phase,
+                                                    const unsigned long long *s_tab,
+                                                    int table_smem,
+                                                    const unsigned long long *g_tab,
+                                                    unsigned long long (&s_ij)[TPT]) {
+    if (tab_all)
+        segment_entropy<SPB, TPT, true, OVL>(my_cnt, stride_s, stride_j, n_phase, s_tab,
+                                             table_smem, g_tab, s_ij);
+    else
+        segment_entropy<SPB, TPT, false, OVL>(my_cnt, stride_s, stride_j, n_phase, s_tab,
+                                              table_smem, g_tab, s_ij);
+}
+
+// Chan et al.'s pairwise update of (count, mean, M2) moments.
+__device__ __forceinline__ void chan_merge(double &n, double &mean, double &m2, double nb,
+                                           double meanb, double m2b) {
+    if (nb <= 0.0) return;
+    if (n <= 0.0) {
+        n = nb;
+        mean = meanb;
+        m2 = m2b;
+        return;
+    }
+    const double tot = n + nb;
+    const double d = meanb - mean;
+    mean += d * (nb / tot);
+    m2 += m2b + d * d * (n * nb / tot);
+    n = tot;
 }
 
 template <int MODE, int TPT, int LOG2B>
@@ -212,7 +269,8 @@ __global__ void __launch_bounds__(1 << LOG2B, (LOG2B >= 9 ? 2 : (LOG2B == 8 ? 4 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n_phase = a.n_phase, n_mag = a.n_mag;
     constexpr int SPB = slots_per_bin(MODE);
-    const int n_slots = SPB * n_phase;
+    const int ovl = a.overlap ? 1 : 0;
+    const int n_slots = SPB * n_phase + ovl;
     const int stride_j = B, stride_s = n_slots * B;
 
     point_t *s_pts = reinterpret_cast<point_t *>(smem);
@@ -221,6 +279,7 @@ __global__ void __launch_bounds__(1 << LOG2B, (LOG2B >= 9 ? 2 : (LOG2B == 8 ? 4 
     int *s_seg = reinterpret_cast<int *>(s_cnt + TPT * n_slots * B);
     unsigned long long *s_top =
         reinterpret_cast<unsigned long long *>(s_seg + ((n_mag + 2) & ~1));
+    double *s_stat = reinterpret_cast<double *>(s_top + (B / 32) * (a.k > 0 ? a.k : 1));
 
     for (int i = tid; i < a.table_smem; i += B) s_tab[i] = a.table[i];
 
@@ -231,7 +290,7 @@ __global__ void __launch_bounds__(1 << LOG2B, (LOG2B >= 9 ? 2 : (LOG2B == 8 ? 4 
     unsigned int base[TPT];
 #pragma unroll
     for (int s = 0; s < TPT; ++s)
-        base[s] = (unsigned int)__cvta_generic_to_shared(my_cnt + s * stride_s) -
+        base[s] = (unsigned int)__cvta_generic_to_shared(my_cnt + s * stride_s + ovl * B) -
                   ((unsigned int)Fold<MODE>::kSlotBias << SH);
 
     int staged_curve = -1, staged_lo = -1;
@@ -295,46 +354,93 @@ __global__ void __launch_bounds__(1 << LOG2B, (LOG2B >= 9 ? 2 : (LOG2B == 8 ? 4 
                 if (ka < kb) {
                     compiler_fence();
                     const typename ModeTraits<MODE>::point_t *pp = s_pts;
+                    const bool ov = ovl != 0;
                     if (k0) {
-                        if (pdot) count_points<MODE, TPT, SH, true, true>(pp, ka - lo, kb - lo, tc, base, fk);
-                        else count_points<MODE, TPT, SH, false, true>(pp, ka - lo, kb - lo, tc, base, fk);
+                        if (pdot) count_points_ovl<MODE, TPT, SH, true, true>(ov, pp, ka - lo, kb - lo, tc, base, fk);
+                        else count_points_ovl<MODE, TPT, SH, false, true>(ov, pp, ka - lo, kb - lo, tc, base, fk);
                     } else if (MODE == GCE_PHASE_FIXED32) {
-                        if (pdot) count_points<MODE, TPT, SH, true, false>(pp, ka - lo, kb - lo, tc, base, fk);
-                        else count_points<MODE, TPT, SH, false, false>(pp, ka - lo, kb - lo, tc, base, fk);
+                        if (pdot) count_points_ovl<MODE, TPT, SH, true, false>(ov, pp, ka - lo, kb - lo, tc, base, fk);
+                        else count_points_ovl<MODE, TPT, SH, false, false>(ov, pp, ka - lo, kb - lo, tc, base, fk);
                     }
                     compiler_fence();
                 }
                 if (s1 > s0 && s1 > lo && s1 <= hi) {
                     // end of magnitude segment i: c_ij = counter - snapshot
-                    if (tab_all)
-                        segment_entropy<SPB, TPT, true>(my_cnt, stride_s, stride_j, n_phase, s_tab,
-                                                        a.table_smem, a.table, s_ij);
+                    if (ovl)
+                        segment_entropy_any<SPB, TPT, true>(tab_all, my_cnt, stride_s, stride_j,
+                                                            n_phase, s_tab, a.table_smem, a.table,
+                                                            s_ij);
                     else
-                        segment_entropy<SPB, TPT, false>(my_cnt, stride_s, stride_j, n_phase,
-                                                         s_tab, a.table_smem, a.table, s_ij);
+                        segment_entropy_any<SPB, TPT, false>(tab_all, my_cnt, stride_s, stride_j,
+                                                             n_phase, s_tab, a.table_smem, a.table,
+                                                             s_ij);
                 }
             }
         }
 
-        // sum_j c_j ln c_j from the cumulative counters, then H
-        const double inv = kTabInvScale / (double)n;
+        // sum_j c_j ln c_j from the cumulative counters, then H (the counts total
+        // 2N with overlapping bins, every point being in two bins)
+        const double inv = kTabInvScale / (double)(n * (1 + ovl));
         unsigned long long key[TPT];
+        float hv[TPT];
 #pragma unroll
         for (int s = 0; s < TPT; ++s) {
             unsigned long long sj = 0ull;
-            const unsigned int *w = my_cnt + s * stride_s;
+            const unsigned int *w = my_cnt + s * stride_s + ovl * stride_j;
             for (int j = 0; j < n_phase; ++j) {
                 int cj = (int)(w[j * stride_j] & 0xffffu);
                 if (SPB == 2) cj += (int)(w[(j + n_phase) * stride_j] & 0xffffu);
+                if (ovl && j == n_phase - 1) cj += (int)(w[-stride_j] & 0xffffu);
                 sj += tab_lookup<false>(s_tab, a.table_smem, a.table, cj);
             }
             long long d = (long long)(sj - s_ij[s]);
             if (d < 0) d = 0;
             const float h = __double2float_rn(__dmul_rn(__ll2double_rn(d), inv));
+            hv[s] = h;
             key[s] = kNoKey;
             if (tt[s] < a.n_trials) {
                 if (a.out) a.out[(long long)c * a.n_trials + tt[s]] = h;
                 key[s] = ((unsigned long long)__float_as_uint(h) << 32) | (unsigned long long)tt[s];
+            }
+        }
+
+        if (a.stats) {
+            // moments of the tile's H for the significance of Eq. 5: per warp, sums of
+            // H - shift in FP32 (shift = lane 0's first value, so the sums stay small),
+            // then (count, mean, M2) in FP64, merged over the warps in order
+            const float shift = __shfl_sync(0xffffffffu, hv[0], 0);
+            float s1 = 0.f, s2 = 0.f, cnt = 0.f;
+#pragma unroll
+            for (int s = 0; s < TPT; ++s)
+                if (tt[s] < a.n_trials) {
+                    const float dd = hv[s] - shift;
+                    s1 += dd;
+                    s2 = __fmaf_rn(dd, dd, s2);
+                    cnt += 1.f;
+                }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+                s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+                cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+            }
+            if (lane == 0) {
+                const double nw = cnt;
+                const double mu = nw > 0 ? (double)shift + (double)s1 / nw : 0.0;
+                const double m2 = nw > 0 ? fmax((double)s2 - (double)s1 * (double)s1 / nw, 0.0) : 0.0;
+                s_stat[3 * warp] = nw;
+                s_stat[3 * warp + 1] = mu;
+                s_stat[3 * warp + 2] = m2;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                double nn = 0.0, mu = 0.0, m2 = 0.0;
+                for (int w = 0; w < (B >> 5); ++w)
+                    chan_merge(nn, mu, m2, s_stat[3 * w], s_stat[3 * w + 1], s_stat[3 * w + 2]);
+                TileStats *t = a.stats + (long long)c * a.n_tiles + tile;
+                t->n = nn;
+                t->mean = mu;
+                t->m2 = m2;
             }
         }
 
@@ -373,8 +479,10 @@ __global__ void __launch_bounds__(1 << LOG2B, (LOG2B >= 9 ? 2 : (LOG2B == 8 ? 4 
 // Per-curve merge of the tiles' candidates: k rounds of "smallest key above the
 // previous one" (keys are unique: H bits in the high word, trial index low).
 __global__ void k_topk_merge(const unsigned long long *__restrict__ cand, int n_tiles, int k,
-                             float *topk_H, long long *topk_idx, const JobState *st) {
+                             float *topk_H, long long *topk_idx, const TileStats *stats,
+                             double *mean_out, double *std_out, float *rho_out, const JobState *st) {
     __shared__ unsigned long long sh[32];
+    __shared__ double shs[3 * 32];
     if (st->err) return;
     const int c = blockIdx.x;
     const long long n = (long long)n_tiles * k;
@@ -402,6 +510,36 @@ __global__ void k_topk_merge(const unsigned long long *__restrict__ cand, int n_
             topk_idx[(long long)c * k + r] = (long long)(last & 0xffffffffull);
         }
     }
+    if (!stats) return;
+    // Eq. 5: rho = (mu - H_min) / sigma over the curve's whole grid, the tiles'
+    // moments merged in a fixed order (each thread a strided run of tiles, then
+    // a fixed tree), so the result is deterministic
+    double nn = 0.0, mu = 0.0, m2 = 0.0;
+    const TileStats *ts = stats + (long long)c * n_tiles;
+    for (int i = threadIdx.x; i < n_tiles; i += blockDim.x) chan_merge(nn, mu, m2, ts[i].n, ts[i].mean, ts[i].m2);
+    for (int o = 1; o < 32; o <<= 1) {
+        const double nb = __shfl_down_sync(0xffffffffu, nn, o);
+        const double mb = __shfl_down_sync(0xffffffffu, mu, o);
+        const double qb = __shfl_down_sync(0xffffffffu, m2, o);
+        if ((threadIdx.x & (2 * o - 1)) == 0) chan_merge(nn, mu, m2, nb, mb, qb);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        shs[3 * (threadIdx.x >> 5)] = nn;
+        shs[3 * (threadIdx.x >> 5) + 1] = mu;
+        shs[3 * (threadIdx.x >> 5) + 2] = m2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        nn = 0.0;
+        mu = 0.0;
+        m2 = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) chan_merge(nn, mu, m2, shs[3 * w], shs[3 * w + 1], shs[3 * w + 2]);
+        const double sd = nn > 0.0 ? sqrt(m2 / nn) : 0.0;
+        mean_out[c] = mu;
+        std_out[c] = sd;
+        // H_min is the first of the top-k this thread wrote above
+        rho_out[c] = sd > 0.0 ? (float)((mu - (double)topk_H[(long long)c * k]) / sd) : 0.0f;
+    }
 }
 
 // The plain baseline: one launch per curve, one thread per trial, the FP64
@@ -426,6 +564,7 @@ __global__ void __launch_bounds__(256) k_single(MainArgs a, int c) {
         for (int k = s0; k < s1; ++k) {
             const int j = fold_fp64<true>(__ldg(pts + k), tr.x, tr.y, (double)n_phase, n_phase);
             atomicAdd(cnt + j * B, 1u);
+            if (a.overlap) atomicAdd(cnt + (j == 0 ? n_phase - 1 : j - 1) * B, 1u);
         }
         for (int j = 0; j < n_phase; ++j) s_ij += __ldg(a.table + take_segment(cnt + j * B));
     }
@@ -434,8 +573,8 @@ __global__ void __launch_bounds__(256) k_single(MainArgs a, int c) {
     long long d = (long long)(sj - s_ij);
     if (d < 0) d = 0;
     if (valid)
-        a.out[(long long)c * a.n_trials + t] =
-            __double2float_rn(__dmul_rn(__ll2double_rn(d), kTabInvScale / (double)n));
+        a.out[(long long)c * a.n_trials + t] = __double2float_rn(
+            __dmul_rn(__ll2double_rn(d), kTabInvScale / (double)(n * (a.overlap ? 2 : 1))));
 }
 
 // Diagnostic: full 2-D counts of selected cells through the same fold code.
@@ -462,6 +601,7 @@ __global__ void k_counts(MainArgs a, long long n_cells, const long long *cell_cu
                     Fold<MODE>::kSlotBias;
             if (j >= a.n_phase) j -= a.n_phase;  // SPLIT32's second slot of a bin
             out[i * a.n_phase + j] += 1u;
+            if (a.overlap) out[i * a.n_phase + (j == 0 ? a.n_phase - 1 : j - 1)] += 1u;
         }
     }
 }
@@ -498,11 +638,12 @@ cudaError_t launch_for_block(int block, int grid, size_t smem, const MainArgs &a
 }  // namespace
 
 size_t main_smem_bytes(int mode, int block, int tpt, int chunk, int n_phase, int n_mag,
-                       int table_smem, int k) {
+                       int table_smem, int k, int overlap) {
     size_t pt = mode == GCE_PHASE_FP64 ? 8 : 16;
     size_t b = pt * (size_t)chunk + 8 * (size_t)table_smem +
-               4 * (size_t)tpt * slots_per_bin(mode) * n_phase * block +
-               4 * (size_t)((n_mag + 2) & ~1) + 8 * (size_t)(block / 32) * (size_t)(k > 0 ? k : 1);
+               4 * (size_t)tpt * (slots_per_bin(mode) * n_phase + (overlap ? 1 : 0)) * block +
+               4 * (size_t)((n_mag + 2) & ~1) + 8 * (size_t)(block / 32) * (size_t)(k > 0 ? k : 1) +
+               24 * (size_t)(block / 32);
     return b;
 }
 
@@ -540,10 +681,12 @@ cudaError_t launch_main(int mode, int tpt, int block, int grid, size_t smem, con
 }
 
 cudaError_t launch_topk_merge(const unsigned long long *cand, int n_curves, int n_tiles, int k,
-                              float *topk_H, long long *topk_idx, const JobState *st,
+                              float *topk_H, long long *topk_idx, const TileStats *stats,
+                              double *mean, double *std_dev, float *rho, const JobState *st,
                               cudaStream_t s) {
     if (n_curves <= 0) return cudaSuccess;
-    k_topk_merge<<<n_curves, 256, 0, s>>>(cand, n_tiles, k, topk_H, topk_idx, st);
+    k_topk_merge<<<n_curves, 256, 0, s>>>(cand, n_tiles, k, topk_H, topk_idx, stats, mean,
+                                          std_dev, rho, st);
     return cudaGetLastError();
 }
 
@@ -552,7 +695,7 @@ cudaError_t launch_single(const MainArgs &a, int curve, long long, cudaStream_t 
     int B = 256;
     while (B > 32 && single_smem_bytes(a.n_phase, B) > 48 * 1024) B >>= 1;
     const long long g = (a.n_trials + B - 1) / B;
-    const size_t smem = single_smem_bytes(a.n_phase, B);
+    const size_t smem = single_smem_bytes(a.n_phase, B);  // overlap needs no extra slot here
     k_single<<<(unsigned int)g, B, smem, s>>>(a, curve);
     return cudaGetLastError();
 }

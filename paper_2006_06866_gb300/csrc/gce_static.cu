@@ -142,7 +142,8 @@ extern "C" gce_status gce_ce_topk_static(const double *times, const double *mags
     if (chunk > 1024) chunk = 1024;
     int table_smem = (int)(n_max + 1 < 1024 ? n_max + 1 : 1024);
     const size_t smem = main_smem_bytes(mode, block, tpt, chunk, cfg->n_phase_bins,
-                                        cfg->n_mag_bins, table_smem, k);
+                                        cfg->n_mag_bins, table_smem, k,
+                                        (cfg->flags & GCE_FLAG_OVERLAP) ? 1 : 0);
     int optin = 0;
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return fail(GCE_ERR_CUDA, cudaGetErrorString(e));
@@ -211,10 +212,13 @@ extern "C" gce_status gce_ce_topk_static(const double *times, const double *mags
     ma.out = nullptr;
     ma.cand = reinterpret_cast<unsigned long long *>(b + L.cand);
     ma.k = k;
+    ma.stats = nullptr;
+    ma.overlap = (cfg->flags & GCE_FLAG_OVERLAP) ? 1 : 0;
     ma.state = state;
     if ((e = launch_main(mode, tpt, block, (int)grid, smem, ma, s)) != cudaSuccess)
         return fail(GCE_ERR_CUDA, cudaGetErrorString(e));
-    e = launch_topk_merge(ma.cand, n_curves, (int)n_tiles, k, topk_H, (long long *)topk_idx, state, s);
+    e = launch_topk_merge(ma.cand, n_curves, (int)n_tiles, k, topk_H, (long long *)topk_idx,
+                          nullptr, nullptr, nullptr, nullptr, state, s);
     if (e != cudaSuccess) return fail(GCE_ERR_CUDA, cudaGetErrorString(e));
     // device-side input checks: read the flags into host stack memory and wait
     unsigned int err = 0;

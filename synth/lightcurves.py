@@ -28,6 +28,14 @@ parameters, noise):
                 log-spaced periods on 3-60 min x 64 Pdot log-spaced
                 -[1e-13, 1e-10]; 20 phase x 10 mag bins; top-5.
 
+  5 "paper"     the production search of Sec. 3: 100 curves, 10-yr baseline
+                with Gaussian spacing of mean 7 d (Sec. 2.2's VRO-like sampling,
+                n ~ 520); chirping eclipses of a Burdge-like set (Sec. 2.1): P0
+                U(4, 38) min, Pdot log-U over -[1.22e-12, 5.44e-11] (Sec. 3);
+                5,183,995 periods linear in frequency (2/B .. 480 per day, step
+                1/(3B), B = 3600 d) x 32 log-spaced Pdot in -[1e-12, 1e-10];
+                15 x 10 bins; top-5.
+
 Times are float64 seconds from the survey start (t0 = 0).  The paper's own
 catalogs (Sec. 2.1) and its ellc light curves (Sec. 2.2) are not available;
 these draws stand in for them with the shapes above.
@@ -42,7 +50,7 @@ import numpy as np
 from .grids import DAY, linear_frequency_periods, log_periods
 
 SEED_BASE = 20200611
-CONFIG_NAMES = ("plain", "batch", "pdot", "ragged", "longbase")
+CONFIG_NAMES = ("plain", "batch", "pdot", "ragged", "longbase", "paper")
 YEAR_NIGHTS = 365
 SEASON_NIGHTS = 240
 NIGHT_WINDOW = 8 * 3600.0
@@ -290,11 +298,32 @@ def _make_longbase(rng, n_curves=1000, n_periods=100_000, n_pdots=64):
                      topk=5)
 
 
-_MAKERS = (_make_plain, _make_batch, _make_pdot, _make_ragged, _make_longbase)
+def gaussian_cadence(rng, years: float = 10.0, mean_days: float = 7.0, sd_days: float = 1.0):
+    """Sec. 2.2: gaps between observations drawn from a Gaussian of mean mean_days
+    (sd sd_days, truncated at 0.1 d), until the baseline is covered."""
+    span = years * 365.25 * DAY
+    gaps = np.maximum(rng.normal(mean_days, sd_days, int(span / (mean_days * DAY) * 1.2) + 10),
+                      0.1) * DAY
+    t = np.cumsum(gaps)
+    return t[t < span] - 0.0
+
+
+def _make_paper(rng, n_curves=100, n_pdots=32, periods=None):
+    from .grids import paper_frequency_grid, paper_pdot_grid
+    ts = [gaussian_cadence(rng) for _ in range(n_curves)]
+    p0 = rng.uniform(4.0, 38.0, size=n_curves) * 60.0
+    pd = -np.exp(rng.uniform(np.log(1.22e-12), np.log(5.44e-11), size=n_curves))
+    ms = [_eclipse_curve(rng, t, p, d, 0.02) for t, p, d in zip(ts, p0, pd)]
+    per = paper_frequency_grid() if periods is None else periods
+    return _assemble("paper", ts, ms, per, paper_pdot_grid(n_pdots), 15, 10, p0, pd,
+                     np.ones(n_curves), topk=5)
+
+
+_MAKERS = (_make_plain, _make_batch, _make_pdot, _make_ragged, _make_longbase, _make_paper)
 
 
 def make_config(index: int, **overrides) -> LightCurveBatch:
-    """Workload `index` (0..4, see the module docstring), drawn with seed
+    """Workload `index` (0..5, see the module docstring), drawn with seed
     20200611 + index.  Keyword overrides shrink the workload (n_curves, n_obs,
     n_periods, n_pdots where the workload has them) for tests; the draw order
     is unchanged, so a shrunken workload is a prefix-consistent relative of the

@@ -74,3 +74,24 @@ def test_longbase_workload_full(h, mode):
     b = synth.make_config(4)  # 1000 curves x 200-1000 obs x 1e5 periods x 64 Pdot, 20 phase bins
     tH, tI = run_topk(h, b, mode, 5)
     check_curves(b, mode, tH, tI, [11])
+
+
+def test_paper_scale_search(h):
+    """Sec. 3's production search (5,183,995 periods x 32 Pdot, 100 curves of ~520
+    points over ten years): the device's top cells carry the oracle's H, and the
+    significance of Eq. 5 is returned for every curve."""
+    b = synth.make_config(5)
+    cfg = g.Config(15, 10, "split32")
+    g.gce_autotune(h, cfg, int(b.n_obs.max()), b.periods.size * b.pdots.size)
+    tH, tI, mu, sd, rho = g.gce_ce_detect(h, cfg=cfg, k=3, **dev_args(b))
+    assert g.gce_stream_status(h) == g.GCE_OK
+    tH, tI = tH.cpu().numpy().astype(np.float64), tI.cpu().numpy()
+    rho = rho.cpu().numpy()
+    assert np.all(np.isfinite(rho)) and np.all(rho > 0)
+    curves = np.arange(0, 100, 10)
+    cc = np.repeat(curves, 3)
+    ct = tI[curves].ravel()
+    rh, rd, _ = oracle.Oracle().ce_cells(b.times, b.mags, b.offsets, b.periods, b.pdots, 15, 10,
+                                         cc, ct)
+    far = rd > 4 * EPS_PHASE["split32"]
+    assert np.all(np.abs(rh - tH[curves].ravel())[far] <= TOL_H["split32"])

@@ -86,3 +86,14 @@ def test_chirp_phase_law():
         bound = pdot ** 2 * tau ** 3 / (3 * p0 ** 3) * 1.01 + 1e-6
         assert np.all(np.abs(exact - first) <= bound)
     assert np.array_equal(synth.lightcurves.chirp_cycles(tau, 300.0, 0.0), tau / 300.0)
+
+
+def test_paper_workload():
+    """Workload 5: Sec. 3's production grid with Sec. 2.2's ~weekly 10-yr sampling."""
+    b = synth.make_config(5, periods=np.array([600.0, 700.0]))
+    assert b.n_curves == 100 and b.pdots.size == 32
+    assert 480 < b.n_obs.mean() < 560 and b.times.max() < 10 * 365.25 * DAY
+    assert np.all(b.truth_p0 >= 240) and np.all(b.truth_p0 <= 38 * 60)
+    assert np.all(b.truth_pdot < 0)
+    gaps = np.diff(b.curve(0)[0]) / DAY
+    assert 6.5 < gaps.mean() < 7.5
