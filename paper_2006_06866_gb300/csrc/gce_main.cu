@@ -77,11 +77,6 @@ __device__ __forceinline__ FoldConst fold_const(int n_phase, int sh) {
     return k;
 }
 
-// j << s on the integer ALU (a funnel shift), not as a multiply.
-__device__ __forceinline__ unsigned int shl_alu(unsigned int j, int s) {
-    return __funnelshift_l(0u, j, s);
-}
-
 // Fold<MODE> turns a trial's stored constants into the registers its fold
 // needs (prepare) and folds one point into a raw counter slot: the phase bin
 // (FP64, FIXED32) or, for SPLIT32, the bit pattern of the rounding FMA, whose
@@ -193,49 +188,79 @@ __device__ __forceinline__ int take_segment(unsigned int *w) {
     return (int)((nv - v) >> 16);
 }
 
-// End of magnitude segment: add sum_j T(c_ij) of each of the thread's trials.
-// The counters of trial s start at my_cnt + s stride_s (physical slot 0);
-// logical slot l is physical l + ovl, logical slot -1 (overlap only) belongs to
-// the last bin, and with two slots per bin logical j + n_phase belongs to bin j.
-template <int SPB, int TPT, bool ALL_SMEM, bool OVL>
-__device__ __forceinline__ void segment_entropy(unsigned int *my_cnt, int stride_s, int stride_j,
-                                                int n_phase, const unsigned long long *s_tab,
-                                                int table_smem, const unsigned long long *g_tab,
-                                                unsigned long long (&s_ij)[TPT]) {
-#pragma unroll
-    for (int s = 0; s < TPT; ++s) {
-        unsigned int *w = my_cnt + s * stride_s + (OVL ? stride_j : 0);
-        unsigned long long acc = 0ull;
-        if (OVL) {  // logical slot -1: the last bin
-            int c_last = take_segment(w - stride_j);
-            c_last += take_segment(w + (n_phase - 1) * stride_j);
-            if (SPB == 2) c_last += take_segment(w + (2 * n_phase - 1) * stride_j);
-            acc += tab_lookup<ALL_SMEM>(s_tab, table_smem, g_tab, c_last);
+// sum_j T(c_j) over the phase bins, where bin j's count is spread over the
+// logical slots l in [L, R] with l = j (mod n_phase): l, l + n_phase and, only
+// in a window 2 n_phase + 1 slots wide (overlap with every slot live), l +
+// 2 n_phase.  Slot l of a thread's counters is the word w + l stride_j
+// (logical -1 exists with overlapping bins).  SEG: the counts since the last
+// segment end (take_segment, which also moves the snapshot); else the
+// cumulative counts.  Slot values are kept shifted left by 16 until the
+// lookup, so adding a bin's slots needs no extra shift.
+template <bool SEG, bool ALL_SMEM>
+__device__ __forceinline__ unsigned long long bin_window_sum(unsigned int *w, int stride_j,
+                                                             int n_phase, int L, int R,
+                                                             const unsigned long long *s_tab,
+                                                             int table_smem,
+                                                             const unsigned long long *g_tab) {
+    auto get = [&](int l) -> unsigned int {
+        unsigned int *p = w + l * stride_j;
+        if (SEG) {
+            const unsigned int v = *p;
+            const unsigned int nv = __byte_perm(v, 0u, 0x1010);
+            *p = nv;
+            return nv - v;  // (count - snapshot) << 16
         }
-        const int n_j = OVL ? n_phase - 1 : n_phase;
-#pragma unroll 3
-        for (int j = 0; j < n_j; ++j) {
-            int cij = take_segment(w + j * stride_j);
-            if (SPB == 2) cij += take_segment(w + (j + n_phase) * stride_j);
-            acc += tab_lookup<ALL_SMEM>(s_tab, table_smem, g_tab, cij);
-        }
-        s_ij[s] += acc;
+        return *p << 16;
+    };
+    auto lookup = [&](unsigned int d) {
+        return tab_lookup<ALL_SMEM>(s_tab, table_smem, g_tab, (int)(d >> 16));
+    };
+    unsigned long long acc = 0ull;
+    const int last = L + n_phase - 1;  // every bin's first slot lies in [L, last]
+    int l = L;
+    if (R - L >= 2 * n_phase) {
+        acc += lookup(get(l) + get(l + n_phase) + get(l + 2 * n_phase));
+        ++l;
     }
+    const int pe = min(R - n_phase, last);
+#pragma unroll 2
+    for (; l <= pe; ++l) acc += lookup(get(l) + get(l + n_phase));
+#pragma unroll 2
+    for (; l <= last; ++l) acc += lookup(get(l));
+    return acc;
 }
 
-template <int SPB, int TPT, bool OVL>
-__device__ __forceinline__ void segment_entropy_any(bool tab_all, unsigned int *my_cnt,
-                                                    int stride_s, int stride_j, int n_phase,
-                                                    const unsigned long long *s_tab,
-                                                    int table_smem,
-                                                    const unsigned long long *g_tab,
-                                                    unsigned long long (&s_ij)[TPT]) {
-    if (tab_all)
-        segment_entropy<SPB, TPT, true, OVL>(my_cnt, stride_s, stride_j, n_phase, s_tab,
-                                             table_smem, g_tab, s_ij);
-    else
-        segment_entropy<SPB, TPT, false, OVL>(my_cnt, stride_s, stride_j, n_phase, s_tab,
-                                              table_smem, g_tab, s_ij);
+// End of magnitude segment: add sum_j T(c_ij) of each of the thread's trials.
+// wbase[s]: trial s's logical slot 0; live slots [L, R].
+template <int TPT, bool ALL_SMEM>
+__device__ __forceinline__ void segment_entropy(unsigned int *const (&wbase)[TPT], int stride_j,
+                                                int n_phase, int L, int R,
+                                                const unsigned long long *s_tab, int table_smem,
+                                                const unsigned long long *g_tab,
+                                                unsigned long long (&s_ij)[TPT]) {
+#pragma unroll
+    for (int s = 0; s < TPT; ++s)
+        s_ij[s] += bin_window_sum<true, ALL_SMEM>(wbase[s], stride_j, n_phase, L, R, s_tab,
+                                                  table_smem, g_tab);
+}
+
+// fh of a SPLIT32 trial (other modes: unused)
+__device__ __forceinline__ float split_fh(const float4 &t) { return t.x; }
+template <class T>
+__device__ __forceinline__ float split_fh(const T &) { return 0.0f; }
+
+// The slots a SPLIT32 fold can reach.  The fold's residual x obeys |x| <=
+// 1/2 + 2^-23 |th fh| (1 + 2^-22) + 2^-23 without the Pdot term (the two
+// cross terms are each below 2^-24 |th fh|, and three roundings), and |x| <=
+// 1/2 exactly with it (x is re-rounded); the slot is floor(x n + n), monotone
+// in x.  The bound is taken in FP32 with margins (a factor 1.01 and 2^-16)
+// far above its own rounding; cyc_max >= max |tau| f over the warp's trials.
+__device__ __forceinline__ void split_slot_window(bool pdot, float cyc_max, int n_phase, int &zlo,
+                                                  int &zhi) {
+    const float nf = (float)n_phase;
+    const float xm = 0.5f + (pdot ? 0.0f : cyc_max * 1.2040e-7f) + 1.5259e-5f;  // 1.01 2^-23, 2^-16
+    zlo = max((int)floorf(nf - nf * xm), 0);
+    zhi = min((int)floorf(nf + nf * xm), 2 * n_phase - 1);
 }
 
 // Chan et al.'s pairwise update of (count, mean, M2) moments.
@@ -288,10 +313,16 @@ __global__ void __launch_bounds__(1 << LOG2B, (LOG2B >= 9 ? 2 : (LOG2B == 8 ? 4 
     unsigned int *my_cnt = s_cnt + tid;
     const FoldConst fk = fold_const(n_phase, SH);
     unsigned int base[TPT];
+    unsigned int *wbase[TPT];  // logical slot 0 of trial s
 #pragma unroll
-    for (int s = 0; s < TPT; ++s)
-        base[s] = (unsigned int)__cvta_generic_to_shared(my_cnt + s * stride_s + ovl * B) -
+    for (int s = 0; s < TPT; ++s) {
+        wbase[s] = my_cnt + s * stride_s + ovl * B;
+        base[s] = (unsigned int)__cvta_generic_to_shared(wbase[s]) -
                   ((unsigned int)Fold<MODE>::kSlotBias << SH);
+    }
+    // max |tau| of the job (SPLIT32 slot windows), rounded up to FP32
+    const float tau_max_f =
+        SPB == 2 ? __double2float_ru(__longlong_as_double((long long)a.state->tau_max_bits)) : 0.0f;
 
     int staged_curve = -1, staged_lo = -1;
     long long item = 0, item_end = 0;
@@ -333,6 +364,19 @@ __global__ void __launch_bounds__(1 << LOG2B, (LOG2B >= 9 ? 2 : (LOG2B == 8 ? 4 
         }
         const bool pdot = __syncthreads_or(any_pdot) != 0;
         const bool k0 = MODE != GCE_PHASE_FIXED32 || __syncthreads_and(all_k0) != 0;
+        // live logical slots [L, R] of this warp's counters (warp-uniform)
+        int L = -ovl, R = n_phase - 1;
+        if (SPB == 2) {
+            float fm = 0.0f;
+#pragma unroll
+            for (int s = 0; s < TPT; ++s)
+                if (tt[s] < a.n_trials) fm = fmaxf(fm, fabsf(split_fh(tc[s])));
+            fm = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(fm)));
+            int zlo, zhi;
+            split_slot_window(pdot, tau_max_f * fm, n_phase, zlo, zhi);
+            L = zlo - ovl;
+            R = zhi;
+        }
 
         for (int i = 0; i < TPT * n_slots; ++i) my_cnt[i * B] = 0u;
         unsigned long long s_ij[TPT];
@@ -366,14 +410,12 @@ __global__ void __launch_bounds__(1 << LOG2B, (LOG2B >= 9 ? 2 : (LOG2B == 8 ? 4 
                 }
                 if (s1 > s0 && s1 > lo && s1 <= hi) {
                     // end of magnitude segment i: c_ij = counter - snapshot
-                    if (ovl)
-                        segment_entropy_any<SPB, TPT, true>(tab_all, my_cnt, stride_s, stride_j,
-                                                            n_phase, s_tab, a.table_smem, a.table,
-                                                            s_ij);
+                    if (tab_all)
+                        segment_entropy<TPT, true>(wbase, stride_j, n_phase, L, R, s_tab,
+                                                   a.table_smem, a.table, s_ij);
                     else
-                        segment_entropy_any<SPB, TPT, false>(tab_all, my_cnt, stride_s, stride_j,
-                                                             n_phase, s_tab, a.table_smem, a.table,
-                                                             s_ij);
+                        segment_entropy<TPT, false>(wbase, stride_j, n_phase, L, R, s_tab,
+                                                    a.table_smem, a.table, s_ij);
                 }
             }
         }
@@ -385,14 +427,8 @@ __global__ void __launch_bounds__(1 << LOG2B, (LOG2B >= 9 ? 2 : (LOG2B == 8 ? 4 
         float hv[TPT];
 #pragma unroll
         for (int s = 0; s < TPT; ++s) {
-            unsigned long long sj = 0ull;
-            const unsigned int *w = my_cnt + s * stride_s + ovl * stride_j;
-            for (int j = 0; j < n_phase; ++j) {
-                int cj = (int)(w[j * stride_j] & 0xffffu);
-                if (SPB == 2) cj += (int)(w[(j + n_phase) * stride_j] & 0xffffu);
-                if (ovl && j == n_phase - 1) cj += (int)(w[-stride_j] & 0xffffu);
-                sj += tab_lookup<false>(s_tab, a.table_smem, a.table, cj);
-            }
+            const unsigned long long sj = bin_window_sum<false, false>(
+                wbase[s], stride_j, n_phase, L, R, s_tab, a.table_smem, a.table);
             long long d = (long long)(sj - s_ij[s]);
             if (d < 0) d = 0;
             const float h = __double2float_rn(__dmul_rn(__ll2double_rn(d), inv));

@@ -10,7 +10,7 @@ from scipy.stats import entropy as shannon
 import oracle
 import paper_2006_06866_gb300 as g
 import synth
-from gpu_util import dev_args, gpu_grid
+from gpu_util import compare_grid, dev_args, gpu_grid
 
 pytestmark = pytest.mark.gpu
 MODES = ["fp64", "split32", "fixed32"]
@@ -90,7 +90,7 @@ def test_bad_inputs_flagged_on_device(h, mode):
 
 
 def test_out_of_range_fold_is_unsupported(h):
-    """SPLIT32 needs |tau|/P < 2^22 cycles: 1e9 s at a 100 s period is refused."""
+    """SPLIT32 needs |tau|/P < 2^21 cycles: 1e9 s at a 100 s period is refused."""
     b = small_batch(seed=6, n_periods=64)
     args = dev_args(b)
     args["times"] = args["times"] * 12.0
@@ -99,6 +99,33 @@ def test_out_of_range_fold_is_unsupported(h):
     assert g.gce_stream_status(h) == g.GCE_ERR_UNSUPPORTED
     g.gce_ce_grid(h, cfg=g.Config(15, 10, "fixed32"), **args)
     assert g.gce_stream_status(h) == g.GCE_OK
+
+
+@pytest.mark.parametrize("overlap", [False, True])
+def test_split_fold_near_cycle_limit(h, overlap):
+    """The SPLIT32 fold at the edge of its range (up to 0.99 2^21 cycles, where its
+    residual strays farthest from [-1/2, 1/2]), with and without the Pdot term and
+    with phase-bin counts from 2 to 256: every count still reaches the entropy
+    (the epilogue reads only the slots the fold's bound allows), so the grid
+    matches the oracle's."""
+    rng = np.random.default_rng(41)
+    n_obs, n_curves = 300, 3
+    ts = [np.sort(rng.uniform(0.0, 2.0e8, n_obs)) for _ in range(n_curves)]
+    ts[0][-1] = 2.0e8
+    ms = [15 + 0.3 * np.sin(2 * np.pi * t / 97.1) + rng.normal(0, 0.05, n_obs) for t in ts]
+    offs = np.arange(n_curves + 1, dtype=np.int64) * n_obs
+    periods = np.linspace(96.0, 500.0, 257)  # 2e8 s / 96 s = 0.993 2^21 cycles
+    b = synth.LightCurveBatch("edge", np.concatenate(ts), np.concatenate(ms), offs, periods,
+                              np.array([0.0, -1e-13]), 15, 10, np.zeros(n_curves),
+                              np.zeros(n_curves), np.zeros(n_curves))
+    args = dev_args(b)
+    for n_phase in (2, 3, 15, 16, 64, 256):
+        cfg = g.Config(n_phase, 10, "split32", overlap=overlap)
+        got = g.gce_ce_grid(h, cfg=cfg, **args)
+        assert g.gce_stream_status(h) == g.GCE_OK
+        ref, dmin = oracle.Oracle().ce_grid(b.times, b.mags, b.offsets, b.periods, b.pdots,
+                                            n_phase, 10, with_dmin=True, overlap=overlap)
+        compare_grid("split32", got.cpu().numpy().astype(np.float64), ref, dmin)
 
 
 def test_host_checks_raise(h):
