@@ -188,61 +188,79 @@ __device__ __forceinline__ int take_segment(unsigned int *w) {
     return (int)((nv - v) >> 16);
 }
 
-// sum_j T(c_j) over the phase bins, where bin j's count is spread over the
-// logical slots l in [L, R] with l = j (mod n_phase): l, l + n_phase and, only
-// in a window 2 n_phase + 1 slots wide (overlap with every slot live), l +
-// 2 n_phase.  Slot l of a thread's counters is the word w + l stride_j
-// (logical -1 exists with overlapping bins).  SEG: the counts since the last
-// segment end (take_segment, which also moves the snapshot); else the
-// cumulative counts.  Slot values are kept shifted left by 16 until the
-// lookup, so adding a bin's slots needs no extra shift.
-template <bool SEG, bool ALL_SMEM>
-__device__ __forceinline__ unsigned long long bin_window_sum(unsigned int *w, int stride_j,
-                                                             int n_phase, int L, int R,
-                                                             const unsigned long long *s_tab,
-                                                             int table_smem,
-                                                             const unsigned long long *g_tab) {
-    auto get = [&](int l) -> unsigned int {
-        unsigned int *p = w + l * stride_j;
-        if (SEG) {
-            const unsigned int v = *p;
-            const unsigned int nv = __byte_perm(v, 0u, 0x1010);
-            *p = nv;
-            return nv - v;  // (count - snapshot) << 16
-        }
-        return *p << 16;
-    };
-    auto lookup = [&](unsigned int d) {
-        return tab_lookup<ALL_SMEM>(s_tab, table_smem, g_tab, (int)(d >> 16));
-    };
-    unsigned long long acc = 0ull;
-    const int last = L + n_phase - 1;  // every bin's first slot lies in [L, last]
-    int l = L;
-    if (R - L >= 2 * n_phase) {
-        acc += lookup(get(l) + get(l + n_phase) + get(l + 2 * n_phase));
-        ++l;
-    }
-    const int pe = min(R - n_phase, last);
-#pragma unroll 2
-    for (; l <= pe; ++l) acc += lookup(get(l) + get(l + n_phase));
-#pragma unroll 2
-    for (; l <= last; ++l) acc += lookup(get(l));
-    return acc;
-}
+// For each of the thread's TPT trials, sum_j T(c_j) over the phase bins, where
+// bin j's count is spread over the logical slots l in [L, R] with l = j (mod
+// n_phase): l, l + n_phase and, only in a window 2 n_phase + 1 slots wide
+// (overlap with every slot live), l + 2 n_phase.  Trial s's slot l is the word
+// wb[s] + l stride_j (logical -1 exists with overlapping bins).  SEG: the
+// counts since the last segment end, each slot's snapshot moved up to its
+// count (take_segment's update); else the cumulative counts.  Slot values stay
+// shifted left by 16 until the lookup, so a bin's slots add without a shift.
+// Each step loads the counters of a few bins of every trial before it stores
+// any, so the loads overlap instead of waiting on the previous stores.
+template <int TPT, bool SEG, bool ALL_SMEM>
+struct BinWindow {
+    unsigned int *const (&wb)[TPT];
+    const int stride_j;
+    const unsigned long long *s_tab;
+    const int table_smem;
+    const unsigned long long *g_tab;
 
-// End of magnitude segment: add sum_j T(c_ij) of each of the thread's trials.
-// wbase[s]: trial s's logical slot 0; live slots [L, R].
-template <int TPT, bool ALL_SMEM>
-__device__ __forceinline__ void segment_entropy(unsigned int *const (&wbase)[TPT], int stride_j,
-                                                int n_phase, int L, int R,
-                                                const unsigned long long *s_tab, int table_smem,
-                                                const unsigned long long *g_tab,
-                                                unsigned long long (&s_ij)[TPT]) {
+    // G bins starting at first slot l, each with C slots (l, l + n, l + 2n)
+    template <int G, int C>
+    __device__ __forceinline__ void step(int l, int n, unsigned long long (&acc)[TPT]) const {
+        unsigned int *p[TPT][G][C];
+        unsigned int v[TPT][G][C];
 #pragma unroll
-    for (int s = 0; s < TPT; ++s)
-        s_ij[s] += bin_window_sum<true, ALL_SMEM>(wbase[s], stride_j, n_phase, L, R, s_tab,
-                                                  table_smem, g_tab);
-}
+        for (int s = 0; s < TPT; ++s)
+#pragma unroll
+            for (int g = 0; g < G; ++g)
+#pragma unroll
+                for (int k = 0; k < C; ++k) {
+                    p[s][g][k] = wb[s] + (l + g + k * n) * stride_j;
+                    v[s][g][k] = *p[s][g][k];
+                }
+        unsigned long long t[TPT][G];
+#pragma unroll
+        for (int s = 0; s < TPT; ++s)
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                unsigned int d = 0u;
+#pragma unroll
+                for (int k = 0; k < C; ++k)
+                    d += SEG ? __byte_perm(v[s][g][k], 0u, 0x1010) - v[s][g][k] : v[s][g][k] << 16;
+                t[s][g] = tab_lookup<ALL_SMEM>(s_tab, table_smem, g_tab, (int)(d >> 16));
+            }
+        if (SEG) {
+#pragma unroll
+            for (int s = 0; s < TPT; ++s)
+#pragma unroll
+                for (int g = 0; g < G; ++g)
+#pragma unroll
+                    for (int k = 0; k < C; ++k) *p[s][g][k] = __byte_perm(v[s][g][k], 0u, 0x1010);
+        }
+#pragma unroll
+        for (int s = 0; s < TPT; ++s)
+#pragma unroll
+            for (int g = 0; g < G; ++g) acc[s] += t[s][g];
+    }
+
+    __device__ __forceinline__ void sum(int n, int L, int R, unsigned long long (&acc)[TPT]) const {
+        const int last = L + n - 1;  // every bin's first slot lies in [L, last]
+        int l = L;
+        if (R - L >= 2 * n) {
+            step<1, 3>(l, n, acc);
+            ++l;
+        }
+        // about four counters in flight per step
+        constexpr int GP = TPT == 1 ? 2 : 1, GS = TPT == 1 ? 4 : 2;
+        const int pe = min(R - n, last);
+        for (; l + GP - 1 <= pe; l += GP) step<GP, 2>(l, n, acc);
+        for (; l <= pe; ++l) step<1, 2>(l, n, acc);
+        for (; l + GS - 1 <= last; l += GS) step<GS, 1>(l, n, acc);
+        for (; l <= last; ++l) step<1, 1>(l, n, acc);
+    }
+};
 
 // fh of a SPLIT32 trial (other modes: unused)
 __device__ __forceinline__ float split_fh(const float4 &t) { return t.x; }
@@ -411,11 +429,11 @@ __global__ void __launch_bounds__(1 << LOG2B, (LOG2B >= 9 ? 2 : (LOG2B == 8 ? 4 
                 if (s1 > s0 && s1 > lo && s1 <= hi) {
                     // end of magnitude segment i: c_ij = counter - snapshot
                     if (tab_all)
-                        segment_entropy<TPT, true>(wbase, stride_j, n_phase, L, R, s_tab,
-                                                   a.table_smem, a.table, s_ij);
+                        BinWindow<TPT, true, true>{wbase, stride_j, s_tab, a.table_smem, a.table}
+                            .sum(n_phase, L, R, s_ij);
                     else
-                        segment_entropy<TPT, false>(wbase, stride_j, n_phase, L, R, s_tab,
-                                                    a.table_smem, a.table, s_ij);
+                        BinWindow<TPT, true, false>{wbase, stride_j, s_tab, a.table_smem, a.table}
+                            .sum(n_phase, L, R, s_ij);
                 }
             }
         }
@@ -423,12 +441,14 @@ __global__ void __launch_bounds__(1 << LOG2B, (LOG2B >= 9 ? 2 : (LOG2B == 8 ? 4 
         // sum_j c_j ln c_j from the cumulative counters, then H (the counts total
         // 2N with overlapping bins, every point being in two bins)
         const double inv = kTabInvScale / (double)(n * (1 + ovl));
-        unsigned long long key[TPT];
+        unsigned long long key[TPT], sjs[TPT];
         float hv[TPT];
 #pragma unroll
+        for (int s = 0; s < TPT; ++s) sjs[s] = 0ull;
+        BinWindow<TPT, false, false>{wbase, stride_j, s_tab, a.table_smem, a.table}.sum(n_phase, L, R, sjs);
+#pragma unroll
         for (int s = 0; s < TPT; ++s) {
-            const unsigned long long sj = bin_window_sum<false, false>(
-                wbase[s], stride_j, n_phase, L, R, s_tab, a.table_smem, a.table);
+            const unsigned long long sj = sjs[s];
             long long d = (long long)(sj - s_ij[s]);
             if (d < 0) d = 0;
             const float h = __double2float_rn(__dmul_rn(__ll2double_rn(d), inv));
