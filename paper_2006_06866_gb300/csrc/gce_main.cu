@@ -33,14 +33,16 @@ namespace {
 
 constexpr unsigned long long kNoKey = ~0ull;
 
-__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
-        v = w < v ? w : v;
-    }
-    return v;
+// Warp minimum of (H bits, trial index) keys by two single-instruction warp
+// reductions: the smallest high word, then the smallest low word among the
+// lanes holding it (the same order as the 64-bit key).
+__device__ __forceinline__ unsigned long long warp_min_key(unsigned long long v) {
+    const unsigned int hi = (unsigned int)(v >> 32);
+    const unsigned int mh = __reduce_min_sync(0xffffffffu, hi);
+    const unsigned int ml = __reduce_min_sync(0xffffffffu, hi == mh ? (unsigned int)v : 0xffffffffu);
+    return ((unsigned long long)mh << 32) | ml;
 }
+
 
 // c ln c from the fixed-point table: shared memory when every count of the curve
 // is covered there (ALL_SMEM), else shared below table_smem and global above.
@@ -507,7 +509,7 @@ __global__ void __launch_bounds__(1 << LOG2B, (LOG2B >= 9 ? 2 : (LOG2B == 8 ? 4 
                 unsigned long long mine = key[0];
 #pragma unroll
                 for (int s = 1; s < TPT; ++s) mine = key[s] < mine ? key[s] : mine;
-                const unsigned long long m = warp_min_u64(mine);
+                const unsigned long long m = warp_min_key(mine);
                 if (lane == 0) s_top[warp * a.k + r] = m;
 #pragma unroll
                 for (int s = 0; s < TPT; ++s)
@@ -520,7 +522,7 @@ __global__ void __launch_bounds__(1 << LOG2B, (LOG2B >= 9 ? 2 : (LOG2B == 8 ? 4 
                 for (int r = 0; r < a.k; ++r) {
                     unsigned long long mine = kNoKey;
                     for (int i = lane; i < tot; i += 32) mine = s_top[i] < mine ? s_top[i] : mine;
-                    const unsigned long long m = warp_min_u64(mine);
+                    const unsigned long long m = warp_min_key(mine);
                     for (int i = lane; i < tot; i += 32)
                         if (s_top[i] == m) s_top[i] = kNoKey;
                     __syncwarp();
@@ -550,12 +552,12 @@ __global__ void k_topk_merge(const unsigned long long *__restrict__ cand, int n_
             const unsigned long long v = src[i];
             if ((r == 0 || v > last) && v < mine) mine = v;
         }
-        mine = warp_min_u64(mine);
+        mine = warp_min_key(mine);
         if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mine;
         __syncthreads();
         if (threadIdx.x < 32) {
             unsigned long long v = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : kNoKey;
-            v = warp_min_u64(v);
+            v = warp_min_key(v);
             if (threadIdx.x == 0) sh[0] = v;
         }
         __syncthreads();
