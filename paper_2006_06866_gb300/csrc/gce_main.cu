@@ -194,7 +194,7 @@ __device__ __forceinline__ int take_segment(unsigned int *w) {
 // bin j's count is spread over the logical slots l in [L, R] with l = j (mod
 // n_phase): l, l + n_phase and, only in a window 2 n_phase + 1 slots wide
 // (overlap with every slot live), l + 2 n_phase.  Trial s's slot l is the word
-// wb[s] + l stride_j (logical -1 exists with overlapping bins).  SEG: the
+// wb[s] + (l + off) stride_j (logical -1 exists with overlapping bins).  SEG: the
 // counts since the last segment end, each slot's snapshot moved up to its
 // count (take_segment's update); else the cumulative counts.  Slot values stay
 // shifted left by 16 until the lookup, so a bin's slots add without a shift.
@@ -203,6 +203,7 @@ __device__ __forceinline__ int take_segment(unsigned int *w) {
 template <int TPT, bool SEG, bool ALL_SMEM>
 struct BinWindow {
     unsigned int *const (&wb)[TPT];
+    const int off;  // physical slot of logical slot 0
     const int stride_j;
     const unsigned long long *s_tab;
     const int table_smem;
@@ -219,7 +220,7 @@ struct BinWindow {
             for (int g = 0; g < G; ++g)
 #pragma unroll
                 for (int k = 0; k < C; ++k) {
-                    p[s][g][k] = wb[s] + (l + g + k * n) * stride_j;
+                    p[s][g][k] = wb[s] + (l + off + g + k * n) * stride_j;
                     v[s][g][k] = *p[s][g][k];
                 }
         unsigned long long t[TPT][G];
@@ -300,8 +301,18 @@ __device__ __forceinline__ void chan_merge(double &n, double &mean, double &m2, 
     n = tot;
 }
 
+// CTAs per SM the register allocation is sized for.  SPLIT32 with two trials
+// per thread keeps the most counter slots per thread, so shared memory admits
+// fewer CTAs than elsewhere (three of 256 threads at 15 phase bins); those
+// kernels take the registers that frees (80 at 256 threads) instead of 64.
+constexpr int main_min_blocks(int mode, int tpt, int log2b) {
+    return mode == GCE_PHASE_SPLIT32 && tpt == 2
+               ? (log2b >= 9 ? 2 : (log2b == 8 ? 3 : (log2b == 7 ? 6 : 8)))
+               : (log2b >= 9 ? 2 : (log2b == 8 ? 4 : 8));
+}
+
 template <int MODE, int TPT, int LOG2B>
-__global__ void __launch_bounds__(1 << LOG2B, (LOG2B >= 9 ? 2 : (LOG2B == 8 ? 4 : 8))) k_main(MainArgs a) {
+__global__ void __launch_bounds__(1 << LOG2B, main_min_blocks(MODE, TPT, LOG2B)) k_main(MainArgs a) {
     typedef typename ModeTraits<MODE>::point_t point_t;
     typedef typename ModeTraits<MODE>::trial_t trial_t;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -313,9 +324,11 @@ __global__ void __launch_bounds__(1 << LOG2B, (LOG2B >= 9 ? 2 : (LOG2B == 8 ? 4 
     constexpr int SH = LOG2B + 2;  // log2 of the byte stride between a thread's slots
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n_phase = a.n_phase, n_mag = a.n_mag;
-    constexpr int SPB = slots_per_bin(MODE);
+    constexpr bool SPLIT = MODE == GCE_PHASE_SPLIT32;
     const int ovl = a.overlap ? 1 : 0;
-    const int n_slots = SPB * n_phase + ovl;
+    const SlotRange zr = slot_range(MODE, n_phase);
+    const int n_slots = slots_per_trial(MODE, n_phase, ovl);
+    const int slot_off = ovl - zr.zmin;  // physical index of logical slot l: l + slot_off
     const int stride_j = B, stride_s = n_slots * B;
 
     point_t *s_pts = reinterpret_cast<point_t *>(smem);
@@ -333,16 +346,16 @@ __global__ void __launch_bounds__(1 << LOG2B, (LOG2B >= 9 ? 2 : (LOG2B == 8 ? 4 
     unsigned int *my_cnt = s_cnt + tid;
     const FoldConst fk = fold_const(n_phase, SH);
     unsigned int base[TPT];
-    unsigned int *wbase[TPT];  // logical slot 0 of trial s
+    unsigned int *wbase[TPT];  // physical slot 0 of trial s
 #pragma unroll
     for (int s = 0; s < TPT; ++s) {
-        wbase[s] = my_cnt + s * stride_s + ovl * B;
-        base[s] = (unsigned int)__cvta_generic_to_shared(wbase[s]) -
+        wbase[s] = my_cnt + s * stride_s;
+        base[s] = (unsigned int)__cvta_generic_to_shared(wbase[s]) + ((unsigned int)slot_off << SH) -
                   ((unsigned int)Fold<MODE>::kSlotBias << SH);
     }
     // max |tau| of the job (SPLIT32 slot windows), rounded up to FP32
     const float tau_max_f =
-        SPB == 2 ? __double2float_ru(__longlong_as_double((long long)a.state->tau_max_bits)) : 0.0f;
+        SPLIT ? __double2float_ru(__longlong_as_double((long long)a.state->tau_max_bits)) : 0.0f;
 
     int staged_curve = -1, staged_lo = -1;
     long long item = 0, item_end = 0;
@@ -386,7 +399,7 @@ __global__ void __launch_bounds__(1 << LOG2B, (LOG2B >= 9 ? 2 : (LOG2B == 8 ? 4 
         const bool k0 = MODE != GCE_PHASE_FIXED32 || __syncthreads_and(all_k0) != 0;
         // live logical slots [L, R] of this warp's counters (warp-uniform)
         int L = -ovl, R = n_phase - 1;
-        if (SPB == 2) {
+        if (SPLIT) {
             float fm = 0.0f;
 #pragma unroll
             for (int s = 0; s < TPT; ++s)
@@ -394,8 +407,8 @@ __global__ void __launch_bounds__(1 << LOG2B, (LOG2B >= 9 ? 2 : (LOG2B == 8 ? 4 
             fm = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(fm)));
             int zlo, zhi;
             split_slot_window(pdot, tau_max_f * fm, n_phase, zlo, zhi);
-            L = zlo - ovl;
-            R = zhi;
+            L = max(zlo, zr.zmin) - ovl;
+            R = min(zhi, zr.zmax);
         }
 
         for (int i = 0; i < TPT * n_slots; ++i) my_cnt[i * B] = 0u;
@@ -431,10 +444,10 @@ __global__ void __launch_bounds__(1 << LOG2B, (LOG2B >= 9 ? 2 : (LOG2B == 8 ? 4 
                 if (s1 > s0 && s1 > lo && s1 <= hi) {
                     // end of magnitude segment i: c_ij = counter - snapshot
                     if (tab_all)
-                        BinWindow<TPT, true, true>{wbase, stride_j, s_tab, a.table_smem, a.table}
+                        BinWindow<TPT, true, true>{wbase, slot_off, stride_j, s_tab, a.table_smem, a.table}
                             .sum(n_phase, L, R, s_ij);
                     else
-                        BinWindow<TPT, true, false>{wbase, stride_j, s_tab, a.table_smem, a.table}
+                        BinWindow<TPT, true, false>{wbase, slot_off, stride_j, s_tab, a.table_smem, a.table}
                             .sum(n_phase, L, R, s_ij);
                 }
             }
@@ -447,7 +460,7 @@ __global__ void __launch_bounds__(1 << LOG2B, (LOG2B >= 9 ? 2 : (LOG2B == 8 ? 4 
         float hv[TPT];
 #pragma unroll
         for (int s = 0; s < TPT; ++s) sjs[s] = 0ull;
-        BinWindow<TPT, false, false>{wbase, stride_j, s_tab, a.table_smem, a.table}.sum(n_phase, L, R, sjs);
+        BinWindow<TPT, false, false>{wbase, slot_off, stride_j, s_tab, a.table_smem, a.table}.sum(n_phase, L, R, sjs);
 #pragma unroll
         for (int s = 0; s < TPT; ++s) {
             const unsigned long long sj = sjs[s];
@@ -699,7 +712,7 @@ size_t main_smem_bytes(int mode, int block, int tpt, int chunk, int n_phase, int
                        int table_smem, int k, int overlap) {
     size_t pt = mode == GCE_PHASE_FP64 ? 8 : 16;
     size_t b = pt * (size_t)chunk + 8 * (size_t)table_smem +
-               4 * (size_t)tpt * (slots_per_bin(mode) * n_phase + (overlap ? 1 : 0)) * block +
+               4 * (size_t)tpt * slots_per_trial(mode, n_phase, overlap) * block +
                4 * (size_t)((n_mag + 2) & ~1) + 8 * (size_t)(block / 32) * (size_t)(k > 0 ? k : 1) +
                24 * (size_t)(block / 32);
     return b;
