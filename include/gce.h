@@ -94,7 +94,8 @@ typedef struct {
 } gce_config;
 
 /* Launch shape of the batched kernel.  block: threads per CTA (64, 128, 256
- * or 512); tpt: trials per thread (1 or 2); ctas_per_sm: resident CTAs per SM
+ * or 512); tpt: trials per thread (1, 2, or 4 except with GCE_PHASE_FP64);
+ * ctas_per_sm: resident CTAs per SM
  * (0 = as many as fit); chunk: light-curve points staged in shared memory at
  * once (a multiple of 256, 256 .. 8192). */
 typedef struct {

@@ -127,9 +127,10 @@ static gce_tuning default_tuning(int mode, int n_max) {
     return t;
 }
 
-static bool tuning_ok(const gce_tuning &t) {
+static bool tuning_ok(const gce_tuning &t, int mode) {
     const bool block_ok = t.block == 64 || t.block == 128 || t.block == 256 || t.block == 512;
-    return block_ok && (t.tpt == 1 || t.tpt == 2) && t.ctas_per_sm >= 0 && t.ctas_per_sm <= 32 &&
+    const bool tpt_ok = t.tpt == 1 || t.tpt == 2 || (t.tpt == 4 && mode != GCE_PHASE_FP64);
+    return block_ok && tpt_ok && t.ctas_per_sm >= 0 && t.ctas_per_sm <= 32 &&
            t.chunk >= 256 && t.chunk <= 8192 && t.chunk % 256 == 0;
 }
 
@@ -288,7 +289,7 @@ gce_status make_plan(gce_handle h, const Job &j, Plan &pl) {
     while (pl.smem > (size_t)h->smem_optin) {
         if (pl.chunk > 512) pl.chunk /= 2;
         else if (pl.table_smem > 256) pl.table_smem /= 2;
-        else if (pl.tpt > 1) pl.tpt = 1;
+        else if (pl.tpt > 1) pl.tpt /= 2;
         else if (pl.block > 64) pl.block /= 2;
         else if (pl.chunk > 64) pl.chunk /= 2;
         else break;
@@ -681,7 +682,7 @@ extern "C" gce_status gce_get_tuning(gce_handle h, const gce_config *cfg, int32_
 
 extern "C" gce_status gce_set_tuning(gce_handle h, const gce_config *cfg, int32_t n_obs_hint,
                                      const gce_tuning *t) {
-    if (!h || !cfg || !t || !tuning_ok(*t)) return GCE_ERR_INVALID;
+    if (!h || !cfg || !t || !tuning_ok(*t, cfg->phase_mode)) return GCE_ERR_INVALID;
     h->tune[tune_key(cfg, std::max(1, n_obs_hint))] = *t;
     return GCE_OK;
 }
@@ -721,7 +722,7 @@ extern "C" gce_status gce_autotune(gce_handle h, const gce_config *cfg, int32_t 
     gce_tuning best = default_tuning(cfg->phase_mode, n_obs);
     float best_ms = 1e30f;
     const int blocks[] = {128, 256, 512};
-    const int tpts[] = {1, 2};
+    const int tpts[] = {1, 2, 4};
     const int chunks[] = {512, 1024, 2048};
     gce_config c2 = *cfg;
     c2.flags |= GCE_FLAG_NO_GRAPH;
@@ -742,6 +743,7 @@ extern "C" gce_status gce_autotune(gce_handle h, const gce_config *cfg, int32_t 
             for (int tp : tpts)
                 for (int ch : chunks) {
                     if (ch > 512 && ch >= 2 * n_obs) continue;  // same plan as a smaller chunk
+                    if (tp == 4 && cfg->phase_mode == GCE_PHASE_FP64) continue;  // not built
                     gce_tuning c = default_tuning(cfg->phase_mode, n_obs);
                     c.block = b;
                     c.tpt = tp;

@@ -305,8 +305,11 @@ __device__ __forceinline__ void chan_merge(double &n, double &mean, double &m2, 
 // per thread keeps the most counter slots per thread, so shared memory admits
 // fewer CTAs than elsewhere (three of 256 threads at 15 phase bins); those
 // kernels take the registers that frees (80 at 256 threads) instead of 64.
+// Four trials per thread need four times the counters of one: at most 512
+// threads per SM fit, and those kernels take up to 128 registers.
 constexpr int main_min_blocks(int mode, int tpt, int log2b) {
-    return mode == GCE_PHASE_SPLIT32 && tpt == 2
+    return tpt == 4 ? (log2b >= 9 ? 1 : (log2b == 8 ? 2 : (log2b == 7 ? 4 : 8)))
+           : mode == GCE_PHASE_SPLIT32 && tpt == 2
                ? (log2b >= 9 ? 2 : (log2b == 8 ? 3 : (log2b == 7 ? 6 : 8)))
                : (log2b >= 9 ? 2 : (log2b == 8 ? 4 : 8));
 }
@@ -721,13 +724,15 @@ size_t main_smem_bytes(int mode, int block, int tpt, int chunk, int n_phase, int
 size_t single_smem_bytes(int n_phase, int block) { return 4 * (size_t)n_phase * block; }
 
 const void *main_kernel_ptr(int mode, int tpt, int block) {
-    switch (mode * 4 + tpt) {
-        case GCE_PHASE_FP64 * 4 + 1: return kernel_for_block<GCE_PHASE_FP64, 1>(block);
-        case GCE_PHASE_FP64 * 4 + 2: return kernel_for_block<GCE_PHASE_FP64, 2>(block);
-        case GCE_PHASE_SPLIT32 * 4 + 1: return kernel_for_block<GCE_PHASE_SPLIT32, 1>(block);
-        case GCE_PHASE_SPLIT32 * 4 + 2: return kernel_for_block<GCE_PHASE_SPLIT32, 2>(block);
-        case GCE_PHASE_FIXED32 * 4 + 1: return kernel_for_block<GCE_PHASE_FIXED32, 1>(block);
-        case GCE_PHASE_FIXED32 * 4 + 2: return kernel_for_block<GCE_PHASE_FIXED32, 2>(block);
+    switch (mode * 8 + tpt) {
+        case GCE_PHASE_FP64 * 8 + 1: return kernel_for_block<GCE_PHASE_FP64, 1>(block);
+        case GCE_PHASE_FP64 * 8 + 2: return kernel_for_block<GCE_PHASE_FP64, 2>(block);
+        case GCE_PHASE_SPLIT32 * 8 + 1: return kernel_for_block<GCE_PHASE_SPLIT32, 1>(block);
+        case GCE_PHASE_SPLIT32 * 8 + 2: return kernel_for_block<GCE_PHASE_SPLIT32, 2>(block);
+        case GCE_PHASE_SPLIT32 * 8 + 4: return kernel_for_block<GCE_PHASE_SPLIT32, 4>(block);
+        case GCE_PHASE_FIXED32 * 8 + 1: return kernel_for_block<GCE_PHASE_FIXED32, 1>(block);
+        case GCE_PHASE_FIXED32 * 8 + 2: return kernel_for_block<GCE_PHASE_FIXED32, 2>(block);
+        case GCE_PHASE_FIXED32 * 8 + 4: return kernel_for_block<GCE_PHASE_FIXED32, 4>(block);
         default: return nullptr;
     }
 }
@@ -740,13 +745,15 @@ cudaError_t main_kernel_attrs(int mode, int tpt, int block, size_t smem) {
 
 cudaError_t launch_main(int mode, int tpt, int block, int grid, size_t smem, const MainArgs &a,
                         cudaStream_t s) {
-    switch (mode * 4 + tpt) {
-        case GCE_PHASE_FP64 * 4 + 1: return launch_for_block<GCE_PHASE_FP64, 1>(block, grid, smem, a, s);
-        case GCE_PHASE_FP64 * 4 + 2: return launch_for_block<GCE_PHASE_FP64, 2>(block, grid, smem, a, s);
-        case GCE_PHASE_SPLIT32 * 4 + 1: return launch_for_block<GCE_PHASE_SPLIT32, 1>(block, grid, smem, a, s);
-        case GCE_PHASE_SPLIT32 * 4 + 2: return launch_for_block<GCE_PHASE_SPLIT32, 2>(block, grid, smem, a, s);
-        case GCE_PHASE_FIXED32 * 4 + 1: return launch_for_block<GCE_PHASE_FIXED32, 1>(block, grid, smem, a, s);
-        case GCE_PHASE_FIXED32 * 4 + 2: return launch_for_block<GCE_PHASE_FIXED32, 2>(block, grid, smem, a, s);
+    switch (mode * 8 + tpt) {
+        case GCE_PHASE_FP64 * 8 + 1: return launch_for_block<GCE_PHASE_FP64, 1>(block, grid, smem, a, s);
+        case GCE_PHASE_FP64 * 8 + 2: return launch_for_block<GCE_PHASE_FP64, 2>(block, grid, smem, a, s);
+        case GCE_PHASE_SPLIT32 * 8 + 1: return launch_for_block<GCE_PHASE_SPLIT32, 1>(block, grid, smem, a, s);
+        case GCE_PHASE_SPLIT32 * 8 + 2: return launch_for_block<GCE_PHASE_SPLIT32, 2>(block, grid, smem, a, s);
+        case GCE_PHASE_SPLIT32 * 8 + 4: return launch_for_block<GCE_PHASE_SPLIT32, 4>(block, grid, smem, a, s);
+        case GCE_PHASE_FIXED32 * 8 + 1: return launch_for_block<GCE_PHASE_FIXED32, 1>(block, grid, smem, a, s);
+        case GCE_PHASE_FIXED32 * 8 + 2: return launch_for_block<GCE_PHASE_FIXED32, 2>(block, grid, smem, a, s);
+        case GCE_PHASE_FIXED32 * 8 + 4: return launch_for_block<GCE_PHASE_FIXED32, 4>(block, grid, smem, a, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -128,6 +128,12 @@ def test_split_fold_near_cycle_limit(h, overlap):
         compare_grid("split32", got.cpu().numpy().astype(np.float64), ref, dmin)
 
 
+def test_four_trials_per_thread_not_built_for_fp64(h):
+    with pytest.raises(g.GceError):
+        g.gce_set_tuning(h, g.Config(15, 10, "fp64"), 500, block=128, tpt=4)
+    g.gce_set_tuning(h, g.Config(15, 10, "split32"), 500, block=128, tpt=4)
+
+
 def test_host_checks_raise(h):
     b = small_batch()
     args = dev_args(b)
@@ -183,6 +189,6 @@ def test_autotune_keeps_results(h):
     before = gpu_grid(h, dev_args(b), "fixed32")
     g.gce_autotune(h, cfg, 500, 20000)
     t = g.gce_get_tuning(h, cfg, 500)
-    assert t["block"] in (128, 256, 512) and t["tpt"] in (1, 2)
+    assert t["block"] in (128, 256, 512) and t["tpt"] in (1, 2, 4)
     after = gpu_grid(h, dev_args(b), "fixed32")
     assert np.array_equal(before, after)
