@@ -259,7 +259,7 @@ struct Job {
 
 struct Plan {
     long long n_points, n_trials, n_items;
-    int n_max, n_tiles, block, tpt, grid, chunk, table_smem, grab;
+    int n_max, n_tiles, n_ptiles, pd_major, block, tpt, grid, chunk, table_smem, grab;
     size_t smem;
 };
 
@@ -297,8 +297,10 @@ gce_status make_plan(gce_handle h, const Job &j, Plan &pl) {
     }
     if (pl.smem > (size_t)h->smem_optin)
         return fail(h, GCE_ERR_UNSUPPORTED, "launch shape needs %zu bytes of shared memory", pl.smem);
-    const long long tile = (long long)pl.block * pl.tpt;
-    pl.n_tiles = (int)((pl.n_trials + tile - 1) / tile);
+    const TileGrid tg = tile_grid(j.n_periods, j.n_pdots, pl.block, pl.tpt);
+    pl.n_tiles = (int)tg.n_tiles;
+    pl.n_ptiles = tg.n_ptiles;
+    pl.pd_major = tg.pd_major;
     pl.n_items = (long long)j.n_curves * pl.n_tiles;
     CUDA_TRY(h, main_kernel_attrs(cfg->phase_mode, pl.tpt, pl.block, pl.smem));
     int occ = 0;
@@ -360,7 +362,11 @@ gce_status enqueue(gce_handle h, const Job &j, const Plan &pl, cudaStream_t s, b
     ma.order = (const int *)h->order.p;
     ma.table = (const unsigned long long *)h->table.p;
     ma.n_trials = pl.n_trials;
+    ma.n_periods = j.n_periods;
+    ma.n_pdots = j.n_pdots;
     ma.n_tiles = pl.n_tiles;
+    ma.n_ptiles = pl.n_ptiles;
+    ma.pd_major = pl.pd_major;
     ma.n_items = pl.n_items;
     ma.grab = pl.grab;
     ma.n_phase = cfg->n_phase_bins;

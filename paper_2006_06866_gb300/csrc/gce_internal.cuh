@@ -101,11 +101,14 @@ __host__ __device__ inline void split_balanced(long long x, int *hi, int *lo) {
 // ------------------------------------------------------------------ folds
 
 // Eq. 3 in binary64 with the pinned operation sequence (see gce.h); returns the
-// phase bin.  With pdot == false, a is known to be +-0 and x = s exactly.
+// phase bin.  With pdot == false, a is known to be +-0 and x = s exactly.  The
+// period part s = tau f is split out so that trials sharing the period can
+// share it (fold_fp64_from completes the fold from it).
+__device__ __forceinline__ double fold_fp64_fpart(double tau, double f) { return __dmul_rn(tau, f); }
+
 template <bool PDOT>
-__device__ __forceinline__ int fold_fp64(double tau, double f, double a, double nphi,
-                                         int n_phase) {
-    double s = __dmul_rn(tau, f);
+__device__ __forceinline__ int fold_fp64_from(double s, double tau, double a, double nphi,
+                                              int n_phase) {
     double x = s;
     if (PDOT) {
         double b = __dmul_rn(a, tau);
@@ -114,6 +117,12 @@ __device__ __forceinline__ int fold_fp64(double tau, double f, double a, double 
     double phi = __dsub_rn(x, floor(x));
     int j = __double2int_rd(__dmul_rn(phi, nphi));
     return min(j, n_phase - 1);
+}
+
+template <bool PDOT>
+__device__ __forceinline__ int fold_fp64(double tau, double f, double a, double nphi,
+                                         int n_phase) {
+    return fold_fp64_from<PDOT>(fold_fp64_fpart(tau, f), tau, a, nphi, n_phase);
 }
 
 // Eq. 3 in FP32 double-float.  tau = th + tl and f = fh + fl (float pairs),
@@ -130,29 +139,40 @@ __device__ __forceinline__ int fold_fp64(double tau, double f, double a, double 
 // Phase error about 1e-7 cycles (a few 2^-25 roundings).
 constexpr float kRound = 12582912.0f;  // 1.5 * 2^23
 
-template <bool PDOT>
-__device__ __forceinline__ int fold_split(float4 pt, float4 tr, float nphi, float zoff) {
+// The period part of the fold, shared by trials of the same period: th fh with
+// its integer cycles removed, plus the cross terms (the whole residual x when
+// Pdot = 0).
+__device__ __forceinline__ float fold_split_fpart(float4 pt, float4 tr) {
     const float th = pt.x, tl = pt.y;
     const float fh = tr.x, fl = tr.y;
     const float t = __fmaf_rn(th, fh, kRound);
-    float r = __fmaf_rn(th, fh, __fsub_rn(kRound, t));
-    float x;
+    const float r = __fmaf_rn(th, fh, __fsub_rn(kRound, t));
+    return __fmaf_rn(th, fl, __fmaf_rn(tl, fh, r));
+}
+
+// The rest of the fold from the period part c: the Pdot term -a tau^2 reduced
+// the same way, the sum reduced once more, then the slot.
+template <bool PDOT>
+__device__ __forceinline__ int fold_split_from(float c, float4 pt, float4 tr, float nphi,
+                                               float zoff) {
+    float x = c;
     if (PDOT) {
         const float t2h = pt.z, t2l = pt.w;
         const float nah = tr.z, nal = tr.w;  // -a split
         const float t2 = __fmaf_rn(nah, t2h, kRound);
         const float r2 = __fmaf_rn(nah, t2h, __fsub_rn(kRound, t2));
-        float c = __fmaf_rn(tl, fh, r);
-        c = __fmaf_rn(th, fl, c);
         c = __fmaf_rn(nah, t2l, c);
         c = __fmaf_rn(nal, t2h, c);
         const float y = __fadd_rn(c, r2);
         x = __fsub_rn(y, __fsub_rn(__fadd_rn(y, kRound), kRound));
-    } else {
-        x = __fmaf_rn(th, fl, __fmaf_rn(tl, fh, r));
     }
     const float z = __fmaf_rd(x, nphi, zoff);  // zoff = 1.5 2^23 + n_phase
     return __float_as_int(z) - __float_as_int(kRound);
+}
+
+template <bool PDOT>
+__device__ __forceinline__ int fold_split(float4 pt, float4 tr, float nphi, float zoff) {
+    return fold_split_from<PDOT>(fold_split_fpart(pt, tr), pt, tr, nphi, zoff);
 }
 
 // Eq. 3 in 32-bit-limb fixed point, the phase in units of 2^-32 cycles so that
@@ -210,35 +230,20 @@ __device__ __forceinline__ FixedPrep fixed_prep(const FixedTrial &t) {
     return p;
 }
 
-template <bool PDOT>
-__device__ __forceinline__ unsigned int fold_fixed_phase(uint4 pt, const FixedPrep &t) {
+// The period part of the fixed-point fold, shared by trials of the same period:
+// the exact integer products of T and F, with the offset C.
+__device__ __forceinline__ unsigned int fold_fixed_fpart(uint4 pt, const FixedPrep &t) {
     const int T1 = (int)pt.x;
-    unsigned int acc = mad_lo_u32((unsigned int)T1, t.F1, t.C);
-    acc = mad_hi_s32(T1, t.F0, acc);
-    float zin = t.K;
-    if (PDOT) {
-        const unsigned int U1 = pt.z;
-        acc = mad_lo_u32(U1, t.A1, acc);
-        acc = mad_hi_u32(t.A0, U1, acc);
-        zin = __fmaf_rn(__uint_as_float(pt.w), t.G2, zin);
-    }
-    const float z = __fmaf_rn(__uint_as_float(pt.y), t.G0, zin);
-    return acc + (__float_as_uint(z) << t.k);
+    const unsigned int acc = mad_lo_u32((unsigned int)T1, t.F1, t.C);
+    return mad_hi_s32(T1, t.F0, acc);
 }
 
-template <bool PDOT>
-__device__ __forceinline__ int fold_fixed(uint4 pt, const FixedPrep &t, unsigned int n_phase) {
-    return (int)__umulhi(fold_fixed_phase<PDOT>(pt, t), n_phase);
-}
-
-// Same fold, specialised for K0 (the shift by k is zero: every trial of the
-// tile has F1 < 2^22), returning the phase bin.
+// The rest of the fold from the period part acc: the Pdot products, the FP32
+// cross terms and, for the bin, the multiply-high by n_phase.  K0: the shift
+// by k is zero (every trial of the tile has F1 < 2^22).
 template <bool PDOT, bool K0>
-__device__ __forceinline__ unsigned int fold_fixed_bin(uint4 pt, const FixedPrep &t,
-                                                       unsigned int n_phase) {
-    const int T1 = (int)pt.x;
-    unsigned int acc = mad_lo_u32((unsigned int)T1, t.F1, t.C);
-    acc = mad_hi_s32(T1, t.F0, acc);
+__device__ __forceinline__ unsigned int fold_fixed_phase_from(unsigned int acc, uint4 pt,
+                                                              const FixedPrep &t) {
     float zin = t.K;
     if (PDOT) {
         const unsigned int U1 = pt.z;
@@ -247,13 +252,24 @@ __device__ __forceinline__ unsigned int fold_fixed_bin(uint4 pt, const FixedPrep
         zin = __fmaf_rn(__uint_as_float(pt.w), t.G2, zin);
     }
     const unsigned int zb = __float_as_uint(__fmaf_rn(__uint_as_float(pt.y), t.G0, zin));
-    acc += K0 ? zb : __funnelshift_l(0u, zb, t.k);
-    return __umulhi(acc, n_phase);
+    return acc + (K0 ? zb : __funnelshift_l(0u, zb, t.k));
+}
+
+template <bool PDOT>
+__device__ __forceinline__ int fold_fixed(uint4 pt, const FixedPrep &t, unsigned int n_phase) {
+    return (int)__umulhi(fold_fixed_phase_from<PDOT, false>(fold_fixed_fpart(pt, t), pt, t),
+                         n_phase);
+}
+
+template <bool PDOT, bool K0>
+__device__ __forceinline__ unsigned int fold_fixed_bin_from(unsigned int acc, uint4 pt,
+                                                            const FixedPrep &t,
+                                                            unsigned int n_phase) {
+    return __umulhi(fold_fixed_phase_from<PDOT, K0>(acc, pt, t), n_phase);
 }
 
 // ------------------------------------------------------------------ entropy
 
-// Phase-bin slots per trial in the counters: SPLIT32 uses two per bin.
 // The counter slots a trial keeps: logical slots [zmin, zmax] (plus logical
 // -1 below them with overlapping bins).  FP64 and FIXED32 count phase bins
 // directly.  SPLIT32's slot is floor(x n + n) for the fold residual x; a job
@@ -313,6 +329,28 @@ struct TileStats {
     double n, mean, m2;
 };
 
+// Trial tiles of one curve's grid for a launch of `block` threads x `tpt`
+// trials.  With several Pdot values and tpt > 1 a tile is block periods x tpt
+// consecutive Pdot values, so that a thread's trials share their period (and
+// the fold's period part); otherwise a tile is a run of block x tpt flat trial
+// indices q n_periods + p.
+struct TileGrid {
+    long long n_tiles;
+    int n_ptiles, pd_major;
+};
+inline TileGrid tile_grid(long long n_periods, long long n_pdots, int block, int tpt) {
+    TileGrid g;
+    g.pd_major = (n_pdots > 1 && tpt > 1) ? 1 : 0;
+    if (g.pd_major) {
+        g.n_ptiles = (int)((n_periods + block - 1) / block);
+        g.n_tiles = (long long)g.n_ptiles * ((n_pdots + tpt - 1) / tpt);
+    } else {
+        g.n_ptiles = 0;
+        g.n_tiles = (n_periods * n_pdots + (long long)block * tpt - 1) / ((long long)block * tpt);
+    }
+    return g;
+}
+
 struct MainArgs {
     const void *payload;
     const long long *offsets;
@@ -321,7 +359,10 @@ struct MainArgs {
     const int *order;          // curves in processing order (longest first)
     const unsigned long long *table;
     long long n_trials;
+    int n_periods, n_pdots;
     int n_tiles;               // trial tiles per curve
+    int n_ptiles;              // period-major tiling: tiles along the periods
+    int pd_major;              // tile = block periods x tpt Pdot values (else flat runs)
     long long n_items;         // n_curves * n_tiles
     int grab;                  // items taken per work-counter increment
     int n_phase;

@@ -85,35 +85,57 @@ __device__ __forceinline__ FoldConst fold_const(int n_phase, int sh) {
 // offset kSlotBias is removed once from the counter base address instead of
 // per point.  raw - kSlotBias is the bin, or for SPLIT32 the bin or the bin
 // plus n_phase (two slots per bin).
+// fpart / offset_from split the fold at its period part (what trials of the same
+// period share); offset is the two composed, so every path folds identically.
 template <int MODE> struct Fold;
 template <> struct Fold<GCE_PHASE_FP64> {
     typedef double2 prep_t;
+    typedef double fpart_t;
     static constexpr int kSlotBias = 0;
     __device__ __forceinline__ static prep_t prepare(double2 t) { return t; }
     template <bool PDOT>
     __device__ __forceinline__ static int raw_slot(double p, const prep_t &t, const FoldConst &k) {
         return fold_fp64<PDOT>(p, t.x, t.y, k.nphi_d, k.n_phase);
     }
+    __device__ __forceinline__ static fpart_t fpart(double p, const prep_t &t) {
+        return fold_fp64_fpart(p, t.x);
+    }
+    template <bool PDOT, bool K0, int SH>
+    __device__ __forceinline__ static unsigned int offset_from(fpart_t f, double p,
+                                                               const prep_t &t,
+                                                               const FoldConst &k) {
+        return (unsigned int)fold_fp64_from<PDOT>(f, p, t.y, k.nphi_d, k.n_phase) << SH;
+    }
     template <bool PDOT, bool K0, int SH>
     __device__ __forceinline__ static unsigned int offset(double p, const prep_t &t,
                                                           const FoldConst &k) {
-        return (unsigned int)raw_slot<PDOT>(p, t, k) << SH;
+        return offset_from<PDOT, K0, SH>(fpart(p, t), p, t, k);
     }
     __device__ __forceinline__ static bool has_pdot(double2 t) { return t.y != 0.0; }
     __device__ __forceinline__ static bool k_zero(const prep_t &) { return true; }
 };
 template <> struct Fold<GCE_PHASE_SPLIT32> {
     typedef float4 prep_t;
+    typedef float fpart_t;
     static constexpr int kSlotBias = 0x4B400000;  // bits of 1.5 2^23
     __device__ __forceinline__ static prep_t prepare(float4 t) { return t; }
     template <bool PDOT>
     __device__ __forceinline__ static int raw_slot(float4 p, const prep_t &t, const FoldConst &k) {
         return fold_split<PDOT>(p, t, k.nphi_f, k.zoff) + kSlotBias;
     }
+    __device__ __forceinline__ static fpart_t fpart(float4 p, const prep_t &t) {
+        return fold_split_fpart(p, t);
+    }
+    template <bool PDOT, bool K0, int SH>
+    __device__ __forceinline__ static unsigned int offset_from(fpart_t f, float4 p,
+                                                               const prep_t &t,
+                                                               const FoldConst &k) {
+        return (unsigned int)(fold_split_from<PDOT>(f, p, t, k.nphi_f, k.zoff) + kSlotBias) << SH;
+    }
     template <bool PDOT, bool K0, int SH>
     __device__ __forceinline__ static unsigned int offset(float4 p, const prep_t &t,
                                                           const FoldConst &k) {
-        return (unsigned int)raw_slot<PDOT>(p, t, k) << SH;
+        return offset_from<PDOT, K0, SH>(fpart(p, t), p, t, k);
     }
     __device__ __forceinline__ static bool has_pdot(float4 t) {
         return t.z != 0.0f || t.w != 0.0f;
@@ -122,16 +144,25 @@ template <> struct Fold<GCE_PHASE_SPLIT32> {
 };
 template <> struct Fold<GCE_PHASE_FIXED32> {
     typedef FixedPrep prep_t;
+    typedef unsigned int fpart_t;
     static constexpr int kSlotBias = 0;
     __device__ __forceinline__ static prep_t prepare(const FixedTrial &t) { return fixed_prep(t); }
     template <bool PDOT>
     __device__ __forceinline__ static int raw_slot(uint4 p, const prep_t &t, const FoldConst &k) {
         return fold_fixed<PDOT>(p, t, (unsigned int)k.n_phase);
     }
+    __device__ __forceinline__ static fpart_t fpart(uint4 p, const prep_t &t) {
+        return fold_fixed_fpart(p, t);
+    }
+    template <bool PDOT, bool K0, int SH>
+    __device__ __forceinline__ static unsigned int offset_from(fpart_t f, uint4 p, const prep_t &t,
+                                                               const FoldConst &k) {
+        return fold_fixed_bin_from<PDOT, K0>(f, p, t, (unsigned int)k.n_phase) << SH;
+    }
     template <bool PDOT, bool K0, int SH>
     __device__ __forceinline__ static unsigned int offset(uint4 p, const prep_t &t,
                                                           const FoldConst &k) {
-        return fold_fixed_bin<PDOT, K0>(p, t, (unsigned int)k.n_phase) << SH;
+        return offset_from<PDOT, K0, SH>(fpart(p, t), p, t, k);
     }
     __device__ __forceinline__ static bool has_pdot(const FixedTrial &t) {
         return (t.i.z | t.i.w) != 0u;
@@ -153,7 +184,9 @@ __device__ __forceinline__ void compiler_fence() { asm volatile("" ::: "memory")
 // slot bias (mod 2^32); a slot's word is base + (raw << SH), SH = log2(4 block).
 // With OVL (50 %-overlapping phase bins, Sec. 2.3) each point also counts in
 // the bin below, the word one slot stride lower (logical slot -1 exists).
-template <int MODE, int TPT, int SH, bool PDOT, bool K0, bool OVL>
+// SHARED: the thread's trials share their period (period-major tiles), so the
+// fold's period part is computed once per point for all of them.
+template <int MODE, int TPT, int SH, bool PDOT, bool K0, bool OVL, bool SHARED>
 __device__ __forceinline__ void count_points(
     const typename ModeTraits<MODE>::point_t *__restrict__ pts, int ka, int kb,
     const typename Fold<MODE>::prep_t (&tc)[TPT], const unsigned int (&base)[TPT],
@@ -161,10 +194,13 @@ __device__ __forceinline__ void count_points(
 #pragma unroll 4
     for (int k = ka; k < kb; ++k) {
         const typename ModeTraits<MODE>::point_t p = pts[k];
+        typename Fold<MODE>::fpart_t fp{};
+        if (SHARED) fp = Fold<MODE>::fpart(p, tc[0]);
 #pragma unroll
         for (int s = 0; s < TPT; ++s) {
             const unsigned int addr =
-                base[s] + Fold<MODE>::template offset<PDOT, K0, SH>(p, tc[s], fk);
+                base[s] + (SHARED ? Fold<MODE>::template offset_from<PDOT, K0, SH>(fp, p, tc[s], fk)
+                                  : Fold<MODE>::template offset<PDOT, K0, SH>(p, tc[s], fk));
             red_shared_inc(addr);
             if (OVL) red_shared_inc(addr - (1u << SH));
         }
@@ -173,11 +209,17 @@ __device__ __forceinline__ void count_points(
 
 template <int MODE, int TPT, int SH, bool PDOT, bool K0>
 __device__ __forceinline__ void count_points_ovl(
-    bool ovl, const typename ModeTraits<MODE>::point_t *__restrict__ pts, int ka, int kb,
-    const typename Fold<MODE>::prep_t (&tc)[TPT], const unsigned int (&base)[TPT],
+    bool ovl, bool shared, const typename ModeTraits<MODE>::point_t *__restrict__ pts, int ka,
+    int kb, const typename Fold<MODE>::prep_t (&tc)[TPT], const unsigned int (&base)[TPT],
     const FoldConst &fk) {
-    if (ovl) count_points<MODE, TPT, SH, PDOT, K0, true>(pts, ka, kb, tc, base, fk);
-    else count_points<MODE, TPT, SH, PDOT, K0, false>(pts, ka, kb, tc, base, fk);
+    constexpr bool SH_OK = PDOT && TPT > 1;  // sharing pays only with a Pdot term
+    if (SH_OK && shared) {
+        if (ovl) count_points<MODE, TPT, SH, PDOT, K0, true, SH_OK>(pts, ka, kb, tc, base, fk);
+        else count_points<MODE, TPT, SH, PDOT, K0, false, SH_OK>(pts, ka, kb, tc, base, fk);
+    } else {
+        if (ovl) count_points<MODE, TPT, SH, PDOT, K0, true, false>(pts, ka, kb, tc, base, fk);
+        else count_points<MODE, TPT, SH, PDOT, K0, false, false>(pts, ka, kb, tc, base, fk);
+    }
 }
 
 // c_ij of one phase bin at the end of a magnitude segment (low - snapshot), with
@@ -387,9 +429,23 @@ __global__ void __launch_bounds__(1 << LOG2B, main_min_blocks(MODE, TPT, LOG2B))
         typename Fold<MODE>::prep_t tc[TPT];
         long long tt[TPT];
         bool any_pdot = false, all_k0 = true;
+        // trial indices (n_trials marks a slot past the grid): a run of B x TPT
+        // flat indices, or B periods x TPT Pdot values (period-major tiles)
+        const bool pdm = a.pd_major != 0;
+        long long p_idx = 0;
+        int q_base = 0;
+        if (pdm) {
+            p_idx = (long long)(tile % a.n_ptiles) * B + tid;
+            q_base = (tile / a.n_ptiles) * TPT;
+        }
 #pragma unroll
         for (int s = 0; s < TPT; ++s) {
-            tt[s] = (long long)tile * (B * TPT) + (long long)s * B + tid;
+            if (pdm)
+                tt[s] = (p_idx < a.n_periods && q_base + s < a.n_pdots)
+                            ? (long long)(q_base + s) * a.n_periods + p_idx
+                            : a.n_trials;
+            else
+                tt[s] = (long long)tile * (B * TPT) + (long long)s * B + tid;
             trial_t tr{};
             if (tt[s] < a.n_trials) {
                 tr = g_tr[tt[s]];
@@ -436,11 +492,11 @@ __global__ void __launch_bounds__(1 << LOG2B, main_min_blocks(MODE, TPT, LOG2B))
                     const typename ModeTraits<MODE>::point_t *pp = s_pts;
                     const bool ov = ovl != 0;
                     if (k0) {
-                        if (pdot) count_points_ovl<MODE, TPT, SH, true, true>(ov, pp, ka - lo, kb - lo, tc, base, fk);
-                        else count_points_ovl<MODE, TPT, SH, false, true>(ov, pp, ka - lo, kb - lo, tc, base, fk);
+                        if (pdot) count_points_ovl<MODE, TPT, SH, true, true>(ov, pdm, pp, ka - lo, kb - lo, tc, base, fk);
+                        else count_points_ovl<MODE, TPT, SH, false, true>(ov, pdm, pp, ka - lo, kb - lo, tc, base, fk);
                     } else if (MODE == GCE_PHASE_FIXED32) {
-                        if (pdot) count_points_ovl<MODE, TPT, SH, true, false>(ov, pp, ka - lo, kb - lo, tc, base, fk);
-                        else count_points_ovl<MODE, TPT, SH, false, false>(ov, pp, ka - lo, kb - lo, tc, base, fk);
+                        if (pdot) count_points_ovl<MODE, TPT, SH, true, false>(ov, pdm, pp, ka - lo, kb - lo, tc, base, fk);
+                        else count_points_ovl<MODE, TPT, SH, false, false>(ov, pdm, pp, ka - lo, kb - lo, tc, base, fk);
                     }
                     compiler_fence();
                 }

@@ -148,7 +148,8 @@ extern "C" gce_status gce_ce_topk_static(const double *times, const double *mags
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return fail(GCE_ERR_CUDA, cudaGetErrorString(e));
     if (smem > (size_t)optin) return fail(GCE_ERR_UNSUPPORTED, "bin counts too large for this entry point");
-    const long long n_tiles = (n_trials + (long long)block * tpt - 1) / ((long long)block * tpt);
+    const TileGrid tg = tile_grid(n_periods, n_pdots, block, tpt);
+    const long long n_tiles = tg.n_tiles;
     const int point_bytes = mode == GCE_PHASE_FP64 ? 8 : 16;
     const Layout L = layout(n_points, n_curves, n_trials, cfg->n_mag_bins, point_bytes, n_tiles, k);
     if (L.end > kScratchBytes)
@@ -202,7 +203,11 @@ extern "C" gce_status gce_ce_topk_static(const double *times, const double *mags
     ma.order = order;
     ma.table = reinterpret_cast<const unsigned long long *>(b);
     ma.n_trials = n_trials;
+    ma.n_periods = n_periods;
+    ma.n_pdots = n_pdots;
     ma.n_tiles = (int)n_tiles;
+    ma.n_ptiles = tg.n_ptiles;
+    ma.pd_major = tg.pd_major;
     ma.n_items = n_items;
     ma.grab = 1;
     ma.n_phase = cfg->n_phase_bins;
