@@ -31,16 +31,22 @@ sys.path.insert(0, ROOT)
 
 METRIC = "folded point-trials/s (N_obs×N_P×N_Ṗ) on 1 GB300; FP64 vs split-FP32 phase"
 UNIT = "point-trials/s"
-# Algorithmic arithmetic of each fold per point-trial without Pdot, and the pipe
-# that executes it (lanes per clock per SM, from the unit counts of the part):
+# Roofline of k_main.  The FP32 folds are bound by instruction issue (ncu: issue
+# slots ~82 % busy, no pipe above ~60 %): the peak is 4 schedulers x 32 lanes =
+# 128 thread-instructions per clock per SM, and the algorithmic work is the
+# instructions a thread-per-trial fold cannot avoid per point-trial -- the
+# fold's arithmetic, one slot address and one shared-memory increment:
 #   split32: 6 FP32 operations (rounding FMA, subtract, residual FMA, two cross
-#            FMAs, bin FMA) on the FP32 pipe, 128 lanes/clk/SM;
-#   fixed32: one 32-bit multiply-add (1 slot) and two multiply-highs (2 slots
-#            each: half rate) on the integer-multiply pipe, 64 slots/clk/SM;
-#   fp64:    5 FP64 operations (mul, floor, sub, mul, convert), 2 lanes/clk/SM.
-OPS_PER_PT = {"split32": 6, "fixed32": 5, "fp64": 5}
-PIPE = {"split32": ("FP32 pipe", 128), "fixed32": ("integer-multiply pipe (slots)", 64),
-        "fp64": ("FP64 pipe", 2)}
+#            FMAs, bin FMA); with Pdot 15 (the Pdot product reduced the same
+#            way, two more cross FMAs, the sum reduced once more);
+#   fixed32: multiply-add, multiply-high, cross FMA, add, bin multiply-high;
+#            with Pdot 8 (two more integer products, one more cross FMA).
+# The FP64 fold is bound by the FP64 pipe (2 lanes/clk/SM): 5 FP64 operations
+# (mul, floor, sub, mul, convert), 7 with Pdot (mul, FMA).
+FOLD_OPS = {"split32": (6, 15), "fixed32": (5, 8), "fp64": (5, 7)}
+ISSUE_LANES = 128
+FP32_LANES = 128
+FP64_LANES = 2
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 
@@ -407,18 +413,26 @@ def main():
 
     roof = None
     if kern_ms:
-        ops = OPS_PER_PT[args.mode] * pt_step
-        achieved = ops / (kern_ms / 1e3) / 1e9
-        pipe, lanes = PIPE[args.mode]
-        peak = SM_COUNT * lanes * SM_MAX_MHZ * 1e6 / 1e9
+        has_pdot = bool(np.any(batch.pdots != 0.0))
+        fold = FOLD_OPS[args.mode][1 if has_pdot else 0]
+        rate = pt_step / (kern_ms / 1e3)
+        clk = SM_COUNT * SM_MAX_MHZ * 1e6
+        if args.mode == "fp64":
+            ops, lanes, pipe = fold, FP64_LANES, "FP64 pipe"
+        else:
+            ops, lanes = fold + 2, ISSUE_LANES
+            pipe = "issue slots (fold arithmetic + slot address + shared increment)"
+        achieved = ops * rate / 1e9
+        peak = lanes * clk / 1e9
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s",
                 "frac": achieved / peak,
                 "traffic": profiled_traffic(args.mode, args.workload, batch.n_curves),
-                "kernel": "k_main", "kernel_ms": kern_ms,
-                "kernel_point_trials_per_s": pt_step / (kern_ms / 1e3),
+                "kernel": "k_main", "kernel_ms": kern_ms, "kernel_point_trials_per_s": rate,
                 "pipe": pipe,
                 "peak_basis": f"{SM_COUNT} SMs x {lanes} lanes/clk x {SM_MAX_MHZ:.0f} MHz",
-                "ops_per_point_trial": OPS_PER_PT[args.mode]}
+                "ops_per_point_trial": ops}
+        if args.mode == "split32":
+            roof["fp32_pipe_frac"] = fold * rate / (FP32_LANES * clk)
 
     if rank == 0:
         line = {

@@ -143,8 +143,8 @@ double oracle_entropy(const int64_t *counts, int32_t n_mag, int32_t n_phase)
 /* 2-D histogram of one curve for one (P, Pdot) trial, plus the smallest
  * distance (in cycles) of any folded phase from a phase-bin edge.
  * mag_bins: the curve's magnitude bins (oracle_mag_bins).  counts: n_mag*n_phase,
- * overwritten.  overlap != 0 reads Sec. 2.3's "each bin has a 50% overlap with
- * each adjacent bin" as phase bins of width 2/n_phase starting at j/n_phase
+ * overwritten.  overlap != 0 takes Sec. 2.3's half-overlapping neighbouring
+ * phase bins as phase bins of width 2/n_phase starting at j/n_phase
  * (modulo 1): a point in fine bin j then lies in bins j and j - 1 (mod
  * n_phase), and the probabilities of Eq. 4 are counts over their total 2N. */
 static void cell_counts_from_bins(const double *t, const int32_t *mag_bins, int64_t n,
