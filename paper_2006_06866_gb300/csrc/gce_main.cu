@@ -191,7 +191,7 @@ __device__ __forceinline__ void count_points(
     const typename ModeTraits<MODE>::point_t *__restrict__ pts, int ka, int kb,
     const typename Fold<MODE>::prep_t (&tc)[TPT], const unsigned int (&base)[TPT],
     const FoldConst &fk) {
-#pragma unroll 4
+#pragma unroll 8
     for (int k = ka; k < kb; ++k) {
         const typename ModeTraits<MODE>::point_t p = pts[k];
         typename Fold<MODE>::fpart_t fp{};
@@ -343,15 +343,15 @@ __device__ __forceinline__ void chan_merge(double &n, double &mean, double &m2, 
     n = tot;
 }
 
-// CTAs per SM the register allocation is sized for.  SPLIT32 with two trials
-// per thread keeps the most counter slots per thread, so shared memory admits
-// fewer CTAs than elsewhere (three of 256 threads at 15 phase bins); those
-// kernels take the registers that frees (80 at 256 threads) instead of 64.
+// CTAs per SM the register allocation is sized for.  With two trials per
+// thread the FP32 folds' counters already limit shared memory to about three
+// 256-thread CTAs per SM at 15 phase bins, so those kernels take the registers
+// that frees (80 at 256 threads) instead of 64.
 // Four trials per thread need four times the counters of one: at most 512
 // threads per SM fit, and those kernels take up to 128 registers.
 constexpr int main_min_blocks(int mode, int tpt, int log2b) {
     return tpt == 4 ? (log2b >= 9 ? 1 : (log2b == 8 ? 2 : (log2b == 7 ? 4 : 8)))
-           : mode == GCE_PHASE_SPLIT32 && tpt == 2
+           : tpt == 2 && mode != GCE_PHASE_FP64
                ? (log2b >= 9 ? 2 : (log2b == 8 ? 3 : (log2b == 7 ? 6 : 8)))
                : (log2b >= 9 ? 2 : (log2b == 8 ? 4 : 8));
 }
