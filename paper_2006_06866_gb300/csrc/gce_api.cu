@@ -274,9 +274,10 @@ gce_status make_plan(gce_handle h, const Job &j, Plan &pl) {
     pl.block = t.block;
     pl.tpt = t.tpt;
     pl.chunk = std::min(t.chunk, ((pl.n_max + 31) / 32) * 32);
-    // the c ln c table in shared memory covers counts up to the staged chunk
-    // (never fewer than 512); larger counts read it from global memory
-    pl.table_smem = std::min(pl.n_max + 1, std::max(512, pl.chunk));
+    // the c ln c table in shared memory: the whole table when it has at most
+    // 2048 entries (16 KB), so that lookups need no bounds test; longer curves
+    // read counts above it from global memory
+    pl.table_smem = std::min(pl.n_max + 1, 2048);
     const int kk = j.kind == JOB_TOPK ? j.k : 0;
     // shrink the staged chunk, then the table, then trials per thread, then the
     // block, until the CTA fits in shared memory
@@ -729,7 +730,7 @@ extern "C" gce_status gce_autotune(gce_handle h, const gce_config *cfg, int32_t 
     float best_ms = 1e30f;
     const int blocks[] = {128, 256, 512};
     const int tpts[] = {1, 2, 4};
-    const int chunks[] = {512, 1024, 2048};
+    const int chunks[] = {256, 512, 1024, 2048};
     gce_config c2 = *cfg;
     c2.flags |= GCE_FLAG_NO_GRAPH;
     do {
