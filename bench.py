@@ -297,7 +297,7 @@ def main():
             else:
                 g.gce_autotune(h, cfg, int(batch.n_obs.max()),
                                batch.periods.size * batch.pdots.size)
-            tuned[mode] = g.gce_get_tuning(h, cfg, int(batch.n_obs.max()))
+            tuned[mode] = g.gce_get_tuning(h, cfg, int(batch.n_obs.max()), int(batch.pdots.size))
         with torch.cuda.stream(stream):
             for _ in range(warmup):
                 step(mode)

@@ -234,16 +234,21 @@ gce_status gce_kernel_time(gce_handle h, float *ms);
 
 /* Time candidate launch shapes on a synthetic job of the given size and keep
  * the fastest for (phase mode, bins, curve-length bucket) in the handle's
- * cache; later calls with a matching key use it.  Synchronous. */
+ * cache; later calls with a matching key use it.  Jobs with a Pdot axis
+ * (n_pdots > 1, whose tiles pair one period with several Pdot values) are
+ * tuned separately on a synthetic job with 8 Pdot values and cached under
+ * their own entry.  Synchronous. */
 gce_status gce_autotune(gce_handle h, const gce_config *cfg, int32_t n_obs_hint,
                         int64_t n_trials_hint);
 
-/* Read the launch shape the handle would use for a job with this config and
- * typical curve length, or force one (it then replaces the cached choice for
- * that key).  gce_set_tuning returns GCE_ERR_INVALID for shapes outside the
- * documented ranges. */
+/* Read the launch shape the handle would use for a job with this config,
+ * typical curve length and number of Pdot values (n_pdots_hint >= 1; > 1 means
+ * a Pdot axis), or force one (gce_set_tuning replaces the cached choice for
+ * that curve-length bucket, for jobs with and without a Pdot axis).
+ * GCE_ERR_INVALID for n_pdots_hint < 1 or, from gce_set_tuning, for shapes
+ * outside the documented ranges. */
 gce_status gce_get_tuning(gce_handle h, const gce_config *cfg, int32_t n_obs_hint,
-                          gce_tuning *t);
+                          int32_t n_pdots_hint, gce_tuning *t);
 gce_status gce_set_tuning(gce_handle h, const gce_config *cfg, int32_t n_obs_hint,
                           const gce_tuning *t);
 

@@ -70,7 +70,7 @@ SIGNATURES = {
     "gce_stream_status": (_I32, [_P, _P]),
     "gce_kernel_time": (_I32, [_P, ctypes.POINTER(ctypes.c_float)]),
     "gce_autotune": (_I32, [_P, _CFG, _I32, _I64]),
-    "gce_get_tuning": (_I32, [_P, _CFG, _I32, _TUN]),
+    "gce_get_tuning": (_I32, [_P, _CFG, _I32, _I32, _TUN]),
     "gce_set_tuning": (_I32, [_P, _CFG, _I32, _TUN]),
 }
 
@@ -346,11 +346,11 @@ def gce_autotune(handle: Handle, cfg: Config, n_obs_hint: int, n_trials_hint: in
            handle.ptr)
 
 
-def gce_get_tuning(handle: Handle, cfg: Config, n_obs_hint: int):
+def gce_get_tuning(handle: Handle, cfg: Config, n_obs_hint: int, n_pdots: int = 1):
     c = cfg.c()
     t = gce_tuning()
-    _check(lib().gce_get_tuning(handle.ptr, ctypes.byref(c), int(n_obs_hint), ctypes.byref(t)),
-           handle.ptr)
+    _check(lib().gce_get_tuning(handle.ptr, ctypes.byref(c), int(n_obs_hint), int(n_pdots),
+                                ctypes.byref(t)), handle.ptr)
     return {"block": t.block, "tpt": t.tpt, "ctas_per_sm": t.ctas_per_sm, "chunk": t.chunk}
 
 

@@ -26,7 +26,8 @@ struct DevBuf {
     size_t bytes = 0;
 };
 
-typedef std::tuple<int, int, int, int> TuneKey;  // mode, n_phase, n_mag, log2 bucket of N
+// mode, n_phase, n_mag, log2 bucket of N, Pdot axis (n_pdots > 1: period-major tiles)
+typedef std::tuple<int, int, int, int, int> TuneKey;
 
 enum JobKind { JOB_GRID = 0, JOB_TOPK = 1, JOB_SINGLE = 2, JOB_COUNTS = 3 };
 
@@ -134,14 +135,17 @@ static bool tuning_ok(const gce_tuning &t, int mode) {
            t.chunk >= 256 && t.chunk <= 8192 && t.chunk % 256 == 0;
 }
 
-static TuneKey tune_key(const gce_config *cfg, int n_obs) {
+static TuneKey tune_key(const gce_config *cfg, int n_obs, int pd_axis) {
     return TuneKey(cfg->phase_mode, cfg->n_phase_bins, cfg->n_mag_bins,
-                   ilog2_ceil(std::max(n_obs, 1)));
+                   ilog2_ceil(std::max(n_obs, 1)), pd_axis);
 }
 
-static gce_tuning lookup_tuning(gce_handle h, const gce_config *cfg, int n_max) {
-    auto it = h->tune.find(tune_key(cfg, n_max));
+// The cached shape for the key; a Pdot-axis job without its own entry uses the
+// plain one.
+static gce_tuning lookup_tuning(gce_handle h, const gce_config *cfg, int n_max, int pd_axis) {
+    auto it = h->tune.find(tune_key(cfg, n_max, pd_axis));
     if (it != h->tune.end()) return it->second;
+    if (pd_axis) return lookup_tuning(h, cfg, n_max, 0);
     return default_tuning(cfg->phase_mode, n_max);
 }
 
@@ -270,7 +274,7 @@ gce_status make_plan(gce_handle h, const Job &j, Plan &pl) {
     long long nmax = 1;
     for (int c = 0; c < j.n_curves; ++c) nmax = std::max<long long>(nmax, j.h_offsets[c + 1] - j.h_offsets[c]);
     pl.n_max = (int)nmax;
-    const gce_tuning t = j.force ? *j.force : lookup_tuning(h, cfg, pl.n_max);
+    const gce_tuning t = j.force ? *j.force : lookup_tuning(h, cfg, pl.n_max, j.n_pdots > 1 ? 1 : 0);
     pl.block = t.block;
     pl.tpt = t.tpt;
     pl.chunk = std::min(t.chunk, ((pl.n_max + 31) / 32) * 32);
@@ -681,16 +685,17 @@ extern "C" gce_status gce_kernel_time(gce_handle h, float *ms) {
 // ------------------------------------------------------------------ tuning
 
 extern "C" gce_status gce_get_tuning(gce_handle h, const gce_config *cfg, int32_t n_obs_hint,
-                                     gce_tuning *t) {
-    if (!h || !cfg || !t) return GCE_ERR_INVALID;
-    *t = lookup_tuning(h, cfg, std::max(1, n_obs_hint));
+                                     int32_t n_pdots_hint, gce_tuning *t) {
+    if (!h || !cfg || !t || n_pdots_hint < 1) return GCE_ERR_INVALID;
+    *t = lookup_tuning(h, cfg, std::max(1, n_obs_hint), n_pdots_hint > 1 ? 1 : 0);
     return GCE_OK;
 }
 
 extern "C" gce_status gce_set_tuning(gce_handle h, const gce_config *cfg, int32_t n_obs_hint,
                                      const gce_tuning *t) {
     if (!h || !cfg || !t || !tuning_ok(*t, cfg->phase_mode)) return GCE_ERR_INVALID;
-    h->tune[tune_key(cfg, std::max(1, n_obs_hint))] = *t;
+    h->tune[tune_key(cfg, std::max(1, n_obs_hint), 0)] = *t;
+    h->tune[tune_key(cfg, std::max(1, n_obs_hint), 1)] = *t;
     return GCE_OK;
 }
 
@@ -710,7 +715,10 @@ extern "C" gce_status gce_autotune(gce_handle h, const gce_config *cfg, int32_t 
     CUDA_TRY(h, cudaSetDevice(h->device));
     // synthetic job: 3-year times, a square-ish signal, log-spaced periods
     const size_t np = (size_t)n_curves * n_obs;
-    std::vector<double> t(np), m(np), per((size_t)n_tr), pd(1, 0.0);
+    // the Pdot-axis pass: 8 Pdot values linear in [-1e-10, 0] over n_tr / 8 periods
+    const int n_pd = 8;
+    const long long n_trp = std::max<long long>(512, n_tr / n_pd);
+    std::vector<double> t(np), m(np), per((size_t)n_tr), perp((size_t)n_trp), pd(n_pd);
     unsigned long long x = 0x9e3779b97f4a7c15ull;
     auto u01 = [&x]() {
         x ^= x << 13; x ^= x >> 7; x ^= x << 17;
@@ -721,13 +729,15 @@ extern "C" gce_status gce_autotune(gce_handle h, const gce_config *cfg, int32_t 
         m[i] = 15.0 + (u01() < 0.1 ? 0.5 : 0.0) + 0.02 * u01();
     }
     for (long long p = 0; p < n_tr; ++p) per[p] = 300.0 * std::pow(288.0, (double)p / (double)(n_tr - 1));
-    double *d_t = nullptr, *d_m = nullptr, *d_p = nullptr, *d_d = nullptr;
+    for (long long p = 0; p < n_trp; ++p)
+        perp[p] = 300.0 * std::pow(288.0, (double)p / (double)(n_trp - 1));
+    for (int q = 0; q < n_pd; ++q) pd[q] = -1e-10 * (double)q / (double)(n_pd - 1);
+    double *d_t = nullptr, *d_m = nullptr, *d_p = nullptr, *d_pp = nullptr, *d_d = nullptr;
     float *d_out = nullptr;
     cudaStream_t s = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     gce_status result = GCE_OK;
-    gce_tuning best = default_tuning(cfg->phase_mode, n_obs);
-    float best_ms = 1e30f;
+    gce_tuning best[2] = {default_tuning(cfg->phase_mode, n_obs), default_tuning(cfg->phase_mode, n_obs)};
     const int blocks[] = {128, 256, 512};
     const int tpts[] = {1, 2, 4};
     const int chunks[] = {256, 512, 1024, 2048};
@@ -735,7 +745,8 @@ extern "C" gce_status gce_autotune(gce_handle h, const gce_config *cfg, int32_t 
     c2.flags |= GCE_FLAG_NO_GRAPH;
     do {
         if (cudaMalloc(&d_t, 8 * np) || cudaMalloc(&d_m, 8 * np) || cudaMalloc(&d_p, 8 * n_tr) ||
-            cudaMalloc(&d_d, 8) || cudaMalloc(&d_out, 4 * (size_t)n_curves * n_tr) ||
+            cudaMalloc(&d_pp, 8 * n_trp) || cudaMalloc(&d_d, 8 * n_pd) ||
+            cudaMalloc(&d_out, 4 * (size_t)n_curves * std::max(n_tr, n_trp * n_pd)) ||
             cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) || cudaEventCreate(&e0) ||
             cudaEventCreate(&e1)) {
             result = fail(h, GCE_ERR_NOMEM, "autotune: allocation failed");
@@ -744,7 +755,8 @@ extern "C" gce_status gce_autotune(gce_handle h, const gce_config *cfg, int32_t 
         cudaMemcpy(d_t, t.data(), 8 * np, cudaMemcpyHostToDevice);
         cudaMemcpy(d_m, m.data(), 8 * np, cudaMemcpyHostToDevice);
         cudaMemcpy(d_p, per.data(), 8 * n_tr, cudaMemcpyHostToDevice);
-        cudaMemcpy(d_d, pd.data(), 8, cudaMemcpyHostToDevice);
+        cudaMemcpy(d_pp, perp.data(), 8 * n_trp, cudaMemcpyHostToDevice);
+        cudaMemcpy(d_d, pd.data(), 8 * n_pd, cudaMemcpyHostToDevice);
         std::vector<gce_tuning> cands;
         for (int b : blocks)
             for (int tp : tpts)
@@ -757,25 +769,33 @@ extern "C" gce_status gce_autotune(gce_handle h, const gce_config *cfg, int32_t 
                     c.chunk = ch;
                     cands.push_back(c);
                 }
-        for (const gce_tuning &cand : cands) {
-            Job j{};
-            j.kind = JOB_GRID;
-            j.times = d_t; j.mags = d_m; j.h_offsets = offs; j.n_curves = n_curves;
-            j.periods = d_p; j.n_periods = (int)n_tr; j.pdots = d_d; j.n_pdots = 1;
-            j.cfg = &c2; j.out = d_out; j.force = &cand;
-            if (run_job(h, j, s) != GCE_OK) continue;  // shape does not fit: skip it
-            cudaEventRecord(e0, s);
-            for (int rep = 0; rep < 3; ++rep) run_job(h, j, s);
-            cudaEventRecord(e1, s);
-            if (cudaEventSynchronize(e1) != cudaSuccess) {
-                result = fail(h, GCE_ERR_CUDA, "autotune: %s", cudaGetErrorString(cudaGetLastError()));
-                break;
-            }
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best_ms) {
-                best_ms = ms;
-                best = cand;
+        // pass 0: one Pdot value (pd[0] = 0); pass 1: the Pdot axis
+        for (int pass = 0; pass < 2 && result == GCE_OK; ++pass) {
+            float best_ms = 1e30f;
+            for (const gce_tuning &cand : cands) {
+                Job j{};
+                j.kind = JOB_GRID;
+                j.times = d_t; j.mags = d_m; j.h_offsets = offs; j.n_curves = n_curves;
+                if (pass == 0) {
+                    j.periods = d_p; j.n_periods = (int)n_tr; j.pdots = d_d; j.n_pdots = 1;
+                } else {
+                    j.periods = d_pp; j.n_periods = (int)n_trp; j.pdots = d_d; j.n_pdots = n_pd;
+                }
+                j.cfg = &c2; j.out = d_out; j.force = &cand;
+                if (run_job(h, j, s) != GCE_OK) continue;  // shape does not fit: skip it
+                cudaEventRecord(e0, s);
+                for (int rep = 0; rep < 3; ++rep) run_job(h, j, s);
+                cudaEventRecord(e1, s);
+                if (cudaEventSynchronize(e1) != cudaSuccess) {
+                    result = fail(h, GCE_ERR_CUDA, "autotune: %s", cudaGetErrorString(cudaGetLastError()));
+                    break;
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best[pass] = cand;
+                }
             }
         }
     } while (0);
@@ -783,7 +803,10 @@ extern "C" gce_status gce_autotune(gce_handle h, const gce_config *cfg, int32_t 
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (s) cudaStreamDestroy(s);
-    cudaFree(d_t); cudaFree(d_m); cudaFree(d_p); cudaFree(d_d); cudaFree(d_out);
-    if (result == GCE_OK) h->tune[tune_key(cfg, n_obs)] = best;
+    cudaFree(d_t); cudaFree(d_m); cudaFree(d_p); cudaFree(d_pp); cudaFree(d_d); cudaFree(d_out);
+    if (result == GCE_OK) {
+        h->tune[tune_key(cfg, n_obs, 0)] = best[0];
+        h->tune[tune_key(cfg, n_obs, 1)] = best[1];
+    }
     return result;
 }

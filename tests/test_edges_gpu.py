@@ -190,5 +190,11 @@ def test_autotune_keeps_results(h):
     g.gce_autotune(h, cfg, 500, 20000)
     t = g.gce_get_tuning(h, cfg, 500)
     assert t["block"] in (128, 256, 512) and t["tpt"] in (1, 2, 4)
+    tp = g.gce_get_tuning(h, cfg, 500, n_pdots=8)  # tuned separately for a Pdot axis
+    assert tp["block"] in (128, 256, 512) and tp["tpt"] in (1, 2, 4)
     after = gpu_grid(h, dev_args(b), "fixed32")
     assert np.array_equal(before, after)
+    g.gce_set_tuning(h, cfg, 500, block=128, tpt=2, chunk=512)  # forces both entries
+    assert g.gce_get_tuning(h, cfg, 500) == g.gce_get_tuning(h, cfg, 500, n_pdots=8)
+    with pytest.raises(g.GceError):
+        g.gce_get_tuning(h, cfg, 500, n_pdots=0)
