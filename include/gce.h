@@ -76,6 +76,7 @@ typedef enum {
 #define GCE_MAX_MAG_BINS 255
 #define GCE_MAX_CURVE_POINTS 65535
 #define GCE_MAX_TOPK 64
+#define GCE_MAX_BANDS 8
 
 /* flags */
 #define GCE_FLAG_NO_GRAPH 1u      /* launch kernels directly instead of through a CUDA graph */
@@ -162,6 +163,36 @@ gce_status gce_ce_detect(gce_handle h, const double *times, const double *mags,
                          int32_t n_periods, const double *pdots, int32_t n_pdots,
                          const gce_config *cfg, int32_t k, float *topk_H, int64_t *topk_idx,
                          double *mean, double *std, float *rho, void *stream);
+
+/* Multi-filter input (Sec. 2.3): the magnitudes of each light curve come from
+ * up to GCE_MAX_BANDS filters, and each (curve, filter) is normalised on its
+ * own -- its median subtracted, then divided by its standard deviation -- so
+ * that the filters combine into one light curve; the magnitude bins of Sec. 2.3
+ * then span the curve's normalised values.  bands: device uint8[sum N], the
+ * filter index of each point, each < n_bands (1 .. GCE_MAX_BANDS).  Readings:
+ * the median of an even count is the mean of the two middle values, taken as
+ * (a + b) * 0.5; the standard deviation is the population one (ddof 0), with
+ * the mean and the sum of squared deviations accumulated in binary64 in point
+ * order; a filter whose points all share one value (or has one point)
+ * normalises to 0.  A band index >= n_bands is a device-side input error
+ * (GCE_ERR_INVALID from gce_stream_status).  With n_bands == 1 the bins are
+ * those of the curve's own min..max as in gce_ce_grid, up to rounding at bin
+ * edges.  Otherwise as gce_ce_grid. */
+gce_status gce_ce_grid_bands(gce_handle h, const double *times, const double *mags,
+                             const uint8_t *bands, int32_t n_bands, const int64_t *h_offsets,
+                             int32_t n_curves, const double *periods, int32_t n_periods,
+                             const double *pdots, int32_t n_pdots, const gce_config *cfg,
+                             float *out, void *stream);
+
+/* gce_ce_detect on multi-filter input (normalised as in gce_ce_grid_bands).
+ * mean, std and rho may all be NULL: then only the top-k is computed. */
+gce_status gce_ce_detect_bands(gce_handle h, const double *times, const double *mags,
+                               const uint8_t *bands, int32_t n_bands,
+                               const int64_t *h_offsets, int32_t n_curves,
+                               const double *periods, int32_t n_periods, const double *pdots,
+                               int32_t n_pdots, const gce_config *cfg, int32_t k,
+                               float *topk_H, int64_t *topk_idx, double *mean, double *std,
+                               float *rho, void *stream);
 
 /* gce_ce_topk on HOST arrays (h_times, h_mags: sum N float64; h_periods,
  * h_pdots; outputs h_topk_H / h_topk_idx of n_curves * k).  Copies inputs to

@@ -77,6 +77,9 @@ def _bind(lib):
                                     ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
                                     ctypes.c_int64, _I64, _I64, _D, _D, _I64, ctypes.c_int32]
     lib.oracle_ce_cells.restype = ctypes.c_int
+    lib.oracle_band_normalize.argtypes = [_D, ctypes.POINTER(ctypes.c_uint8), ctypes.c_int64,
+                                          ctypes.c_int32, _D]
+    lib.oracle_band_normalize.restype = ctypes.c_int
     return lib
 
 
@@ -132,6 +135,22 @@ class Oracle:
                                  float(pdot), int(n_phase), int(n_mag), int(bool(overlap)),
                                  _p(counts, _I64), ctypes.byref(dmin))
         return h, counts, dmin.value
+
+    def band_normalize(self, mags, bands, offsets, n_bands):
+        """Multi-filter input (Sec. 2.3): every (curve, filter) median/std normalised
+        (oracle_band_normalize, curve by curve).  Raises on a band index >= n_bands."""
+        mags = np.ascontiguousarray(mags, dtype=np.float64)
+        bands = np.ascontiguousarray(bands, dtype=np.uint8)
+        offsets = np.asarray(offsets, dtype=np.int64)
+        out = np.empty_like(mags)
+        for c in range(offsets.shape[0] - 1):
+            lo, hi = int(offsets[c]), int(offsets[c + 1])
+            m, b, o = mags[lo:hi], bands[lo:hi], out[lo:hi]
+            r = self.lib.oracle_band_normalize(_p(m, _D), b.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                                               hi - lo, int(n_bands), _p(o, _D))
+            if r != 0:
+                raise ValueError("band index >= n_bands")
+        return out
 
     # --- batches ------------------------------------------------------------
     def ce_grid(self, times, mags, offsets, periods, pdots, n_phase, n_mag, t0=0.0,

@@ -75,6 +75,54 @@ void oracle_mag_bins(const double *mags, int64_t n, int32_t n_mag, int32_t *bins
     }
 }
 
+/* Multi-filter input (Sec. 2.3): the magnitudes of one curve come from several
+ * filters, and each filter's points are normalised on their own -- the filter's
+ * median subtracted, then divided by the filter's standard deviation -- so that
+ * the filters combine into one light curve before the magnitude bins.
+ * bands[k] < n_bands is the filter of point k; out[k] the normalised value.
+ * Readings of what the paper leaves open: the median of an even count is the
+ * mean of the two middle values, (a + b) * 0.5; the standard deviation is the
+ * population one, sqrt(sum (m - mean)^2 / n) with the mean and the sum taken
+ * in point order; a filter with zero spread normalises to 0.  Returns -1 (and
+ * writes nothing) if a band index is out of range. */
+static int cmp_double(const void *a, const void *b)
+{
+    const double x = *(const double *)a, y = *(const double *)b;
+    return (x < y) ? -1 : (x > y);
+}
+
+int oracle_band_normalize(const double *mags, const uint8_t *bands, int64_t n, int32_t n_bands,
+                          double *out)
+{
+    for (int64_t k = 0; k < n; ++k)
+        if ((int32_t)bands[k] >= n_bands) return -1;
+    double *tmp = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    for (int32_t b = 0; b < n_bands; ++b) {
+        int64_t cnt = 0;
+        for (int64_t k = 0; k < n; ++k)
+            if (MUTANT(11) || bands[k] == b) tmp[cnt++] = mags[k];  /* 11: one set of statistics for all filters */
+        if (cnt == 0) continue;
+        qsort(tmp, (size_t)cnt, sizeof(double), cmp_double);
+        double med = (cnt % 2 == 1) ? tmp[cnt / 2] : (tmp[cnt / 2 - 1] + tmp[cnt / 2]) * 0.5;
+        double sum = 0.0;
+        for (int64_t k = 0; k < n; ++k)
+            if (MUTANT(11) || bands[k] == b) sum += mags[k];
+        const double mean = sum / (double)cnt;
+        if (MUTANT(12)) med = mean;  /* 12: the mean subtracted instead of the median */
+        double ss = 0.0;
+        for (int64_t k = 0; k < n; ++k)
+            if (MUTANT(11) || bands[k] == b) {
+                const double d = mags[k] - mean;
+                ss += d * d;
+            }
+        const double sd = sqrt(ss / (double)cnt);
+        for (int64_t k = 0; k < n; ++k)
+            if (bands[k] == b) out[k] = sd > 0.0 ? (mags[k] - med) / sd : 0.0;
+    }
+    free(tmp);
+    return 0;
+}
+
 /* ---------------------------------------------------------------- trial grid */
 
 /* Per-trial constants of Eq. 3: f = 1/P and a = (1/2 Pdot) f f, so that the

@@ -60,6 +60,10 @@ SIGNATURES = {
     "gce_ce_topk": (_I32, [_P, _P, _P, _HOFF, _I32, _P, _I32, _P, _I32, _CFG, _I32, _P, _P, _P]),
     "gce_ce_detect": (_I32, [_P, _P, _P, _HOFF, _I32, _P, _I32, _P, _I32, _CFG, _I32, _P, _P, _P,
                              _P, _P, _P]),
+    "gce_ce_grid_bands": (_I32, [_P, _P, _P, _P, _I32, _HOFF, _I32, _P, _I32, _P, _I32, _CFG, _P,
+                                 _P]),
+    "gce_ce_detect_bands": (_I32, [_P, _P, _P, _P, _I32, _HOFF, _I32, _P, _I32, _P, _I32, _CFG,
+                                   _I32, _P, _P, _P, _P, _P, _P]),
     "gce_ce_topk_host": (_I32, [_P, _P, _P, _HOFF, _I32, _P, _I32, _P, _I32, _CFG, _I32, _P, _P,
                                 _P]),
     "gce_ce_topk_static": (_I32, [_P, _P, _HOFF, _I32, _P, _I32, _P, _I32, _CFG, _I32, _P, _P,
@@ -251,6 +255,53 @@ def gce_ce_detect(handle: Handle, times, mags, offsets, periods, pdots, cfg: Con
                                _dev(tH, torch.float32, "topk_H"), _dev(tI, torch.int64, "topk_idx"),
                                _dev(mean, torch.float64, "mean"), _dev(std, torch.float64, "std"),
                                _dev(rho, torch.float32, "rho"), _stream(stream)), handle.ptr)
+    return tH, tI, mean, std, rho
+
+
+def gce_ce_grid_bands(handle: Handle, times, mags, bands, n_bands: int, offsets, periods, pdots,
+                      cfg: Config, out=None, stream=None):
+    """gce_ce_grid on multi-filter input: bands is a uint8 CUDA tensor (the filter
+    of each point, < n_bands); each (curve, filter) is median/std normalised."""
+    import torch
+    off, poff, pt, pm, pp, pd = _common(times, mags, offsets, periods, pdots)
+    nc = off.shape[0] - 1
+    if out is None:
+        out = torch.empty((nc, pdots.numel(), periods.numel()), dtype=torch.float32,
+                          device=times.device)
+    c = cfg.c()
+    _check(lib().gce_ce_grid_bands(handle.ptr, pt, pm, _dev(bands, torch.uint8, "bands"),
+                                   int(n_bands), poff, nc, pp, periods.numel(), pd, pdots.numel(),
+                                   ctypes.byref(c), _dev(out, torch.float32, "out"),
+                                   _stream(stream)), handle.ptr)
+    return out
+
+
+def gce_ce_detect_bands(handle: Handle, times, mags, bands, n_bands: int, offsets, periods, pdots,
+                        cfg: Config, k: int, significance=True, stream=None):
+    """gce_ce_detect on multi-filter input; (topk_H, topk_idx, mean, std, rho), the
+    last three None when significance is False."""
+    import torch
+    off, poff, pt, pm, pp, pd = _common(times, mags, offsets, periods, pdots)
+    nc = off.shape[0] - 1
+    dev = times.device
+    tH = torch.empty((nc, k), dtype=torch.float32, device=dev)
+    tI = torch.empty((nc, k), dtype=torch.int64, device=dev)
+    mean = std = rho = None
+    pm_, ps_, pr_ = None, None, None
+    if significance:
+        mean = torch.empty(nc, dtype=torch.float64, device=dev)
+        std = torch.empty(nc, dtype=torch.float64, device=dev)
+        rho = torch.empty(nc, dtype=torch.float32, device=dev)
+        pm_ = _dev(mean, torch.float64, "mean")
+        ps_ = _dev(std, torch.float64, "std")
+        pr_ = _dev(rho, torch.float32, "rho")
+    c = cfg.c()
+    _check(lib().gce_ce_detect_bands(handle.ptr, pt, pm, _dev(bands, torch.uint8, "bands"),
+                                     int(n_bands), poff, nc, pp, periods.numel(), pd,
+                                     pdots.numel(), ctypes.byref(c), int(k),
+                                     _dev(tH, torch.float32, "topk_H"),
+                                     _dev(tI, torch.int64, "topk_idx"), pm_, ps_, pr_,
+                                     _stream(stream)), handle.ptr)
     return tH, tI, mean, std, rho
 
 

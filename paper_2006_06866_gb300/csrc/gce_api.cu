@@ -51,7 +51,7 @@ struct gce_handle_s {
     int smem_optin = 0;
     std::string last_error;
     DevBuf payload, seg, trialc, order, offsets, cand, stats, table, state, in_times, in_mags,
-        in_periods, in_pdots, out_H, out_idx;
+        in_periods, in_pdots, out_H, out_idx, band_stats;
     int table_n = -1;                    // largest count the table covers
     int *h_order = nullptr;              // pinned staging
     long long *h_offsets = nullptr;
@@ -228,7 +228,7 @@ extern "C" gce_status gce_destroy(gce_handle h) {
     for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
     DevBuf *bufs[] = {&h->payload, &h->seg, &h->trialc, &h->order, &h->offsets, &h->cand, &h->stats,
                       &h->table, &h->state, &h->in_times, &h->in_mags, &h->in_periods,
-                      &h->in_pdots, &h->out_H, &h->out_idx};
+                      &h->in_pdots, &h->out_H, &h->out_idx, &h->band_stats};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (h->h_order) cudaFreeHost(h->h_order);
@@ -259,6 +259,8 @@ struct Job {
     const int64_t *cell_curve, *cell_trial;
     uint32_t *counts;
     const gce_tuning *force;     // tuning override (autotuner)
+    const unsigned char *bands;  // multi-filter input (nullptr: one filter, raw magnitudes)
+    int n_bands;
 };
 
 struct Plan {
@@ -358,6 +360,12 @@ gce_status enqueue(gce_handle h, const Job &j, const Plan &pl, cudaStream_t s, b
     pa.payload = h->payload.p;
     pa.seg = (int *)h->seg.p;
     pa.state = st;
+    pa.bands = j.bands;
+    pa.band_stats = (const double2 *)h->band_stats.p;
+    pa.n_bands = j.bands ? j.n_bands : 0;
+    if (j.bands)
+        CUDA_TRY(h, launch_band_stats(j.mags, j.bands, pa.offsets, j.n_curves, j.n_bands,
+                                      (double2 *)h->band_stats.p, st, s));
     CUDA_TRY(h, launch_prep(mode, pa, s));
     MainArgs ma;
     ma.payload = h->payload.p;
@@ -440,6 +448,8 @@ gce_status run_job(gce_handle h, const Job &j, cudaStream_t s) {
         return fail(h, GCE_ERR_INVALID, "significance needs all of mean, std and rho");
     if (j.kind == JOB_COUNTS && j.n_cells > 0 && (!j.cell_curve || !j.cell_trial || !j.counts))
         return fail(h, GCE_ERR_INVALID, "NULL cell array");
+    if (j.bands && (j.n_bands < 1 || j.n_bands > GCE_MAX_BANDS))
+        return fail(h, GCE_ERR_INVALID, "n_bands must be 1 .. %d", GCE_MAX_BANDS);
     CUDA_TRY(h, cudaSetDevice(h->device));
 
     Plan pl;
@@ -453,6 +463,9 @@ gce_status run_job(gce_handle h, const Job &j, cudaStream_t s) {
     if ((st = ensure(h, h->trialc, 32 * (size_t)pl.n_trials)) != GCE_OK) return st;
     if ((st = ensure(h, h->order, sizeof(int) * (size_t)j.n_curves)) != GCE_OK) return st;
     if ((st = ensure(h, h->offsets, sizeof(long long) * (size_t)(j.n_curves + 1))) != GCE_OK) return st;
+    if (j.bands &&
+        (st = ensure(h, h->band_stats, sizeof(double2) * (size_t)j.n_curves * j.n_bands)) != GCE_OK)
+        return st;
     if (j.kind == JOB_TOPK &&
         (st = ensure(h, h->cand, 8 * (size_t)j.n_curves * pl.n_tiles * j.k)) != GCE_OK)
         return st;
@@ -503,7 +516,8 @@ gce_status run_job(gce_handle h, const Job &j, cudaStream_t s) {
             return st;
         }
         if (e != cudaSuccess) return fail(h, GCE_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
-        GraphKey key{j.kind * 4 + (j.rho ? 2 : 0) + ((j.cfg->flags & GCE_FLAG_OVERLAP) ? 1 : 0),
+        GraphKey key{j.kind * 8 + (j.bands ? 4 : 0) + (j.rho ? 2 : 0) +
+                         ((j.cfg->flags & GCE_FLAG_OVERLAP) ? 1 : 0),
                      mode, j.n_curves, j.n_periods, j.n_pdots, j.cfg->n_phase_bins,
                      j.cfg->n_mag_bins, j.k, pl.block, pl.tpt, pl.grid, pl.chunk, pl.table_smem,
                      pl.grab, pl.n_points};
@@ -542,11 +556,12 @@ gce_status run_job(gce_handle h, const Job &j, cudaStream_t s) {
 
 gce_status state_status(gce_handle h) {
     const unsigned int e = h->h_state->err;
-    if (e & (ERR_TIME | ERR_PERIOD | ERR_PDOT))
-        return fail(h, GCE_ERR_INVALID, "device check: %s%s%s",
+    if (e & (ERR_TIME | ERR_PERIOD | ERR_PDOT | ERR_BAND))
+        return fail(h, GCE_ERR_INVALID, "device check: %s%s%s%s",
                     (e & ERR_TIME) ? "non-finite time or magnitude; " : "",
                     (e & ERR_PERIOD) ? "non-finite or non-positive period; " : "",
-                    (e & ERR_PDOT) ? "non-finite period derivative; " : "");
+                    (e & ERR_PDOT) ? "non-finite period derivative; " : "",
+                    (e & ERR_BAND) ? "filter index >= n_bands; " : "");
     if (e & ERR_RANGE)
         return fail(h, GCE_ERR_UNSUPPORTED, "device check: trial range beyond the phase fold's range");
     return GCE_OK;
@@ -593,6 +608,41 @@ extern "C" gce_status gce_ce_detect(gce_handle h, const double *times, const dou
     j.periods = periods; j.n_periods = n_periods; j.pdots = pdots; j.n_pdots = n_pdots;
     j.cfg = cfg; j.k = k; j.topk_H = topk_H; j.topk_idx = topk_idx;
     j.mean = mean; j.std_dev = std_dev; j.rho = rho;
+    return run_job(h, j, (cudaStream_t)stream);
+}
+
+extern "C" gce_status gce_ce_grid_bands(gce_handle h, const double *times, const double *mags,
+                                        const uint8_t *bands, int32_t n_bands,
+                                        const int64_t *h_offsets, int32_t n_curves,
+                                        const double *periods, int32_t n_periods,
+                                        const double *pdots, int32_t n_pdots,
+                                        const gce_config *cfg, float *out, void *stream) {
+    if (!bands) return h ? fail(h, GCE_ERR_INVALID, "NULL band array") : GCE_ERR_INVALID;
+    Job j{};
+    j.kind = JOB_GRID;
+    j.times = times; j.mags = mags; j.h_offsets = h_offsets; j.n_curves = n_curves;
+    j.periods = periods; j.n_periods = n_periods; j.pdots = pdots; j.n_pdots = n_pdots;
+    j.cfg = cfg; j.out = out;
+    j.bands = bands; j.n_bands = n_bands;
+    return run_job(h, j, (cudaStream_t)stream);
+}
+
+extern "C" gce_status gce_ce_detect_bands(gce_handle h, const double *times, const double *mags,
+                                          const uint8_t *bands, int32_t n_bands,
+                                          const int64_t *h_offsets, int32_t n_curves,
+                                          const double *periods, int32_t n_periods,
+                                          const double *pdots, int32_t n_pdots,
+                                          const gce_config *cfg, int32_t k, float *topk_H,
+                                          int64_t *topk_idx, double *mean, double *std_dev,
+                                          float *rho, void *stream) {
+    if (!bands) return h ? fail(h, GCE_ERR_INVALID, "NULL band array") : GCE_ERR_INVALID;
+    Job j{};
+    j.kind = JOB_TOPK;
+    j.times = times; j.mags = mags; j.h_offsets = h_offsets; j.n_curves = n_curves;
+    j.periods = periods; j.n_periods = n_periods; j.pdots = pdots; j.n_pdots = n_pdots;
+    j.cfg = cfg; j.k = k; j.topk_H = topk_H; j.topk_idx = topk_idx;
+    j.mean = mean; j.std_dev = std_dev; j.rho = rho;
+    j.bands = bands; j.n_bands = n_bands;
     return run_job(h, j, (cudaStream_t)stream);
 }
 

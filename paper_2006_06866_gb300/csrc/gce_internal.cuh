@@ -30,6 +30,7 @@ enum : unsigned int {
     ERR_PERIOD = 2u,    // non-finite or non-positive period
     ERR_PDOT = 4u,      // non-finite period derivative
     ERR_RANGE = 8u,     // trial range beyond what the chosen fold represents
+    ERR_BAND = 16u,     // filter index outside [0, n_bands)
 };
 
 // Fixed-point scaling of the FIXED32 fold, derived from the job's maxima.
@@ -313,6 +314,9 @@ struct PrepArgs {
     void *payload;             // ModeTraits<MODE>::point_t[sum N], sorted by mag bin per curve
     int *seg;                  // [n_curves][n_mag + 1] segment starts (relative to the curve)
     const JobState *state;
+    const unsigned char *bands;  // multi-filter input: filter of each point, or nullptr
+    const double2 *band_stats;   // [n_curves][n_bands] {median, standard deviation}
+    int n_bands;
 };
 
 struct TrialArgs {
@@ -384,6 +388,9 @@ cudaError_t launch_scan(const double *times, const double *mags, long long n_poi
                         double t0, JobState *st, cudaStream_t s);
 cudaError_t launch_trials(int mode, const TrialArgs &a, cudaStream_t s);
 cudaError_t launch_prep(int mode, const PrepArgs &a, cudaStream_t s);
+cudaError_t launch_band_stats(const double *mags, const unsigned char *bands,
+                              const long long *offsets, int n_curves, int n_bands,
+                              double2 *stats, JobState *st, cudaStream_t s);
 cudaError_t launch_table(unsigned long long *table, int n_max, cudaStream_t s);
 size_t main_smem_bytes(int mode, int block, int tpt, int chunk, int n_phase, int n_mag,
                        int table_smem, int k, int overlap);

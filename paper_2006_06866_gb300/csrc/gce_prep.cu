@@ -173,6 +173,125 @@ __device__ inline int mag_bin(double m, double mn, double mx, int n_mag) {
     return min(i, n_mag - 1);
 }
 
+// ------------------------------------------------------------------ filters
+
+// Order-preserving map of binary64 to unsigned 64-bit keys (and back).
+__device__ inline unsigned long long f64_key(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ inline double key_f64(unsigned long long k) {
+    return __longlong_as_double((long long)((k >> 63) ? (k & 0x7fffffffffffffffull) : ~k));
+}
+
+// The kth smallest (0-based) magnitude of filter b among the curve's n points:
+// an exact radix selection on the keys, 8 bits per pass from the top, with
+// shared-memory digit histograms.  Every thread returns the value.
+__device__ double band_select(const double *m, const unsigned char *bd, int n, int b, int kth,
+                              unsigned int *hist, unsigned long long *s_pref, int *s_k) {
+    unsigned long long prefix = 0ull;
+    for (int shift = 56; shift >= 0; shift -= 8) {
+        const unsigned long long high = shift == 56 ? 0ull : ~0ull << (shift + 8);
+        for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0u;
+        __syncthreads();
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            if (bd[k] != b) continue;
+            const unsigned long long key = f64_key(m[k]);
+            if ((key & high) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned int cum = 0u;
+            int d = 0;
+            for (; d < 255; ++d) {
+                if (cum + hist[d] > (unsigned int)kth) break;
+                cum += hist[d];
+            }
+            *s_pref = prefix | ((unsigned long long)d << shift);
+            *s_k = kth - (int)cum;
+        }
+        __syncthreads();
+        prefix = *s_pref;
+        kth = *s_k;
+        __syncthreads();
+    }
+    return key_f64(prefix);
+}
+
+// One CTA per curve: for each filter b, the median and the population standard
+// deviation of its magnitudes (the per-filter normalisation of Sec. 2.3), in the
+// operation order stated in gce.h: the median exactly (radix selection), the
+// mean and the sum of squared deviations in binary64 in point order (one
+// thread), so that the normalised values match a plain sequential statement
+// bit for bit.  A filter with no points gets {0, 0}.  Band indices >= n_bands
+// set ERR_BAND.
+__global__ void __launch_bounds__(256) k_band_stats(const double *__restrict__ mags,
+                                                    const unsigned char *__restrict__ bands,
+                                                    const long long *__restrict__ offsets,
+                                                    int n_bands, double2 *stats, JobState *st) {
+    __shared__ unsigned int hist[256];
+    __shared__ unsigned long long s_pref;
+    __shared__ int s_k, s_cnt[GCE_MAX_BANDS];
+    const int c = blockIdx.x;
+    const long long lo = offsets[c];
+    const int n = (int)(offsets[c + 1] - lo);
+    const double *m = mags + lo;
+    const unsigned char *bd = bands + lo;
+    if (threadIdx.x < GCE_MAX_BANDS) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    bool bad = false;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const int b = bd[k];
+        if (b >= n_bands) bad = true;
+        else atomicAdd(&s_cnt[b], 1);
+    }
+    if (__syncthreads_or(bad)) {
+        if (threadIdx.x == 0) atomicOr(&st->err, ERR_BAND);
+        return;
+    }
+    for (int b = 0; b < n_bands; ++b) {
+        const int cnt = s_cnt[b];
+        double2 r = make_double2(0.0, 0.0);
+        if (cnt > 0) {
+            double med = band_select(m, bd, n, b, (cnt - 1) / 2, hist, &s_pref, &s_k);
+            if ((cnt & 1) == 0) {
+                const double hi = band_select(m, bd, n, b, cnt / 2, hist, &s_pref, &s_k);
+                med = __dmul_rn(__dadd_rn(med, hi), 0.5);
+            }
+            if (threadIdx.x == 0) {
+                double sum = 0.0;
+                for (int k = 0; k < n; ++k)
+                    if (bd[k] == b) sum = __dadd_rn(sum, m[k]);
+                const double mean = __ddiv_rn(sum, (double)cnt);
+                double ss = 0.0;
+                for (int k = 0; k < n; ++k)
+                    if (bd[k] == b) {
+                        const double d = __dsub_rn(m[k], mean);
+                        ss = __dadd_rn(ss, __dmul_rn(d, d));
+                    }
+                r = make_double2(med, __dsqrt_rn(__ddiv_rn(ss, (double)cnt)));
+            }
+        }
+        if (threadIdx.x == 0) stats[(long long)c * n_bands + b] = r;
+    }
+}
+
+// The magnitude the bins of Sec. 2.3 see: the raw value, or with multi-filter
+// input (m - median) / sd of the point's filter (0 when sd is 0).
+struct MagView {
+    const double *m;
+    const unsigned char *bd;  // nullptr: raw magnitudes
+    const double2 *bs;        // this curve's {median, sd} per filter
+    int nb;
+    __device__ double operator[](int k) const {
+        if (!bd) return m[k];
+        const int b = bd[k];
+        if (b >= nb) return 0.0;  // flagged by k_band_stats; never read past the table
+        const double2 s = bs[b];
+        return s.y > 0.0 ? __ddiv_rn(__dsub_rn(m[k], s.x), s.y) : 0.0;
+    }
+};
+
 // One CTA per curve: min/max of the magnitudes, magnitude bins, a counting sort
 // of the points by magnitude bin (segment starts written to seg), and the
 // points' fold payload written in the sorted order.  The order of points inside
@@ -185,7 +304,8 @@ __global__ void __launch_bounds__(kPrepBlock) k_prep(PrepArgs a) {
     const int c = blockIdx.x;
     const long long lo = a.offsets[c];
     const int n = (int)(a.offsets[c + 1] - lo);
-    const double *m = a.mags + lo;
+    const MagView m{a.mags + lo, a.bands ? a.bands + lo : nullptr,
+                    a.bands ? a.band_stats + (long long)c * a.n_bands : nullptr, a.n_bands};
     const double *t = a.times + lo;
     double mn = INFINITY, mx = -INFINITY;
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
@@ -285,6 +405,14 @@ cudaError_t launch_trials(int mode, const TrialArgs &a, cudaStream_t s) {
         case GCE_PHASE_SPLIT32: k_trials<GCE_PHASE_SPLIT32><<<g, 256, 0, s>>>(a); break;
         default: k_trials<GCE_PHASE_FIXED32><<<g, 256, 0, s>>>(a); break;
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_band_stats(const double *mags, const unsigned char *bands,
+                              const long long *offsets, int n_curves, int n_bands,
+                              double2 *stats, JobState *st, cudaStream_t s) {
+    if (n_curves <= 0) return cudaSuccess;
+    k_band_stats<<<n_curves, 256, 0, s>>>(mags, bands, offsets, n_bands, stats, st);
     return cudaGetLastError();
 }
 

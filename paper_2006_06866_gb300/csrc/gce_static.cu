@@ -194,6 +194,9 @@ extern "C" gce_status gce_ce_topk_static(const double *times, const double *mags
     pa.payload = b + L.payload;
     pa.seg = reinterpret_cast<int *>(b + L.seg);
     pa.state = state;
+    pa.bands = nullptr;
+    pa.band_stats = nullptr;
+    pa.n_bands = 0;
     if ((e = launch_prep(mode, pa, s)) != cudaSuccess) return fail(GCE_ERR_CUDA, cudaGetErrorString(e));
     MainArgs ma;
     ma.payload = b + L.payload;

@@ -14,11 +14,12 @@ first-order expansion, and the two differ by Pdot^2 tau^3 / (3 P0^3) cycles
 """
 from .grids import (linear_frequency_periods, log_periods, paper_frequency_grid,
                     paper_pdot_grid)
-from .lightcurves import (CONFIG_NAMES, LightCurveBatch, make_config, make_onegrid_injection,
+from .lightcurves import (CONFIG_NAMES, LightCurveBatch, make_config, make_multiband,
+                          make_onegrid_injection,
                           nightly_cadence, sparse_cadence, uniform_cadence)
 
 __all__ = [
-    "CONFIG_NAMES", "LightCurveBatch", "make_config", "make_onegrid_injection",
+    "CONFIG_NAMES", "LightCurveBatch", "make_config", "make_multiband", "make_onegrid_injection",
     "nightly_cadence", "sparse_cadence", "uniform_cadence", "linear_frequency_periods",
     "log_periods", "paper_frequency_grid", "paper_pdot_grid",
 ]

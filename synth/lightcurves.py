@@ -332,6 +332,35 @@ def make_config(index: int, **overrides) -> LightCurveBatch:
     return _MAKERS[int(index)](rng, **overrides)
 
 
+def make_multiband(seed: int, n_curves: int = 40, n_obs: int = 600, n_bands: int = 2,
+                   n_periods: int = 2000, pdots=(0.0,)):
+    """Multi-filter light curves (the filter combination of Sec. 2.3): every visit of
+    a 3-year nightly cadence is in one of n_bands filters, drawn uniformly.  Filter
+    b of a curve shifts its magnitudes by a colour offset U(-0.5, 0.5) mag, scales
+    the eclipse depth by U(0.6, 1.2) and has its own noise sigma U(0.01, 0.05).
+    Eclipsing binaries with P0 log-U(300 s, 3000 s) over log-spaced periods
+    300-3000 s.  Returns (batch, bands uint8[sum N])."""
+    rng = np.random.default_rng(int(seed))
+    ts, ms, bs, p0s = [], [], [], []
+    for _ in range(n_curves):
+        t = nightly_cadence(rng, n_obs)
+        b = rng.integers(0, n_bands, size=t.shape[0])
+        p0 = float(_loguniform(rng, 300.0, 3000.0))
+        depth, width, phase0 = rng.uniform(0.2, 1.0), rng.uniform(0.02, 0.06), rng.uniform(0, 1)
+        colour = rng.uniform(-0.5, 0.5, size=n_bands)
+        gain = rng.uniform(0.6, 1.2, size=n_bands)
+        sigma = rng.uniform(0.01, 0.05, size=n_bands)
+        base = eclipse_signal(chirp_cycles(t, p0, 0.0), depth, width, phase0)
+        m = 15.0 + colour[b] + gain[b] * base + rng.normal(0.0, 1.0, size=t.shape[0]) * sigma[b]
+        ts.append(t)
+        ms.append(m)
+        bs.append(b.astype(np.uint8))
+        p0s.append(p0)
+    batch = _assemble("multiband", ts, ms, log_periods(300.0, 3000.0, n_periods), list(pdots),
+                      15, 10, np.array(p0s), np.zeros(n_curves), np.ones(n_curves), topk=5)
+    return batch, np.concatenate(bs)
+
+
 def make_onegrid_injection(seed: int, n_curves: int, n_obs: int, periods, pdots,
                            kind: str = "eclipse", years: float = 3.0, noise: float = 0.0):
     """Noiseless (or lightly noisy) signals whose (P0, Pdot) sit exactly on the given

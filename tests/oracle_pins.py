@@ -15,7 +15,9 @@ What each pin leans on (none of it re-types the oracle's own formulas):
     one magnitude bin or one point per phase bin: zero);
   * invariants of Eq. 4 (bounds, permutation invariance);
   * the paper's worked example (Fig. 2: P = 7 min, Pdot = -2.14e-11, ten years
-    of weekly visits) and on-grid recovery of injected signals.
+    of weekly visits) and on-grid recovery of injected signals;
+  * numpy's median and standard deviation for the per-filter normalisation of
+    multi-filter input, and a closed form for a calibrated copy of a filter.
 """
 from __future__ import annotations
 
@@ -476,11 +478,56 @@ def pin_significance(orc):
     return out
 
 
+def pin_band_normalization(orc):
+    """Multi-filter input (Sec. 2.3): every filter of a curve is normalised on its
+    own (median subtracted, divided by the standard deviation).  Library routine:
+    numpy's median and population standard deviation per filter.  Closed form: a
+    second filter that repeats every observation through an exact calibration
+    (2 m + 3, dyadic data, 64 points, so every step is exact) normalises to the
+    same values, and a curve whose every point is seen twice has the one-filter
+    curve's CE grid bit for bit."""
+    rng = np.random.default_rng(47)
+    out = []
+    worst = 0.0
+    for _ in range(40):
+        n = int(rng.integers(1, 200))
+        nb = int(rng.integers(1, 5))
+        m = rng.normal(15, 0.5, n)
+        b = rng.integers(0, nb, n).astype(np.uint8)
+        z = orc.band_normalize(m, b, [0, n], nb)
+        for k in range(nb):
+            x = m[b == k]
+            if x.size == 0:
+                continue
+            sd = x.std()
+            ref = (x - np.median(x)) / sd if sd > 0 else np.zeros_like(x)
+            worst = max(worst, float(np.max(np.abs(z[b == k] - ref))))
+    out.append(("filters: numpy median and population std per filter", worst < 1e-12,
+                f"worst {worst:.3g}"))
+    const = orc.band_normalize(np.full(5, 14.5), np.zeros(5, np.uint8), [0, 5], 1)
+    out.append(("filters: a filter without spread normalises to 0", np.all(const == 0.0), ""))
+    n = 64
+    t = np.sort(rng.uniform(0.0, 1e8, n))
+    m0 = np.round(rng.normal(15.0, 0.3, n) * 1024.0) / 1024.0
+    per = synth.log_periods(300.0, 3000.0, 300)
+    pd = np.array([0.0, -1e-11])
+    z1 = orc.band_normalize(m0, np.zeros(n, np.uint8), [0, n], 1)
+    g1 = orc.ce_grid(t, z1, np.array([0, n]), per, pd, 15, 10)
+    b2 = np.r_[np.zeros(n), np.ones(n)].astype(np.uint8)
+    z2 = orc.band_normalize(np.r_[m0, 2.0 * m0 + 3.0], b2, [0, 2 * n], 2)
+    g2 = orc.ce_grid(np.r_[t, t], z2, np.array([0, 2 * n]), per, pd, 15, 10)
+    out.append(("filters: an affine copy in a second filter normalises identically",
+                np.array_equal(z2[:n], z2[n:]) and np.array_equal(z2[:n], z1), ""))
+    out.append(("filters: every point seen twice leaves the CE grid unchanged",
+                np.array_equal(g1, g2), f"max diff {np.abs(g1 - g2).max():.3g}"))
+    return out
+
+
 ALL_PINS = (
     pin_fold_exact_rational, pin_fold_edges, pin_pdot_zero_plain_fold, pin_eq6_dephasing,
     pin_mag_bins, pin_entropy_chain_rule, pin_entropy_special_cases,
     pin_entropy_bounds_and_invariance, pin_brute_force_tiny, pin_paper_worked_example,
-    pin_recovery, pin_overlapping_bins, pin_significance,
+    pin_recovery, pin_overlapping_bins, pin_significance, pin_band_normalization,
 )
 
 

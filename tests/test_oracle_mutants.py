@@ -1,6 +1,7 @@
 """Every planted mistake in the oracle (a dropped 1/2, a flipped Pdot sign, an
 inverted log ratio, a transposed marginal, round instead of floor, a wrong
-magnitude scale, a wrong normaliser, a wrong epoch sign, a missing 1/P) must
+magnitude scale, a wrong normaliser, a wrong epoch sign, a missing 1/P, one
+normalisation for all filters, the mean for the median) must
 make at least one pin fail.  The mistakes are compiled into separate copies of
 the oracle on the CPU; the real oracle is untouched."""
 import pytest
@@ -18,6 +19,8 @@ MUTANTS = {
     7: "probabilities normalised by n_phase instead of N",
     9: "epoch added instead of subtracted",
     10: "Pdot term missing one factor 1/P",
+    11: "one set of filter statistics for the whole curve",
+    12: "filter mean subtracted instead of its median",
 }
 
 
