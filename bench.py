@@ -68,6 +68,9 @@ def parse():
                     help="total oracle seconds of the reference arm (spread over its steps)")
     ap.add_argument("--curves", type=int, default=0,
                     help="use only the first N curves of the workload (profiling runs)")
+    ap.add_argument("--bands", type=int, default=0,
+                    help="multi-filter input: give every point one of N filters (seeded) and "
+                         "search through gce_ce_detect_bands (0 = single filter)")
     ap.add_argument("--shape", default="",
                     help="block,tpt,chunk: fixed launch shape instead of autotuning (profiling runs)")
     return ap.parse_args()
@@ -282,9 +285,18 @@ def main():
     out_H = torch.empty((batch.n_curves, k), dtype=torch.float32, device=dev)
     out_I = torch.empty((batch.n_curves, k), dtype=torch.int64, device=dev)
 
+    nb = int(args.bands)
+    bands_h = (np.random.default_rng(20200611 + 100 * args.workload + nb)
+               .integers(0, nb, size=batch.times.size).astype(np.uint8) if nb else None)
+    b_d = torch.tensor(bands_h, device=dev) if nb else None
+
     def step(mode, time_kernel=False):
         cfg = g.Config(batch.n_phase, batch.n_mag, mode, t0=batch.t0, time_kernel=time_kernel)
-        g.gce_ce_topk(h, t_d, m_d, offs, p_d, q_d, cfg, k, out_H, out_I, stream=stream)
+        if nb:
+            g.gce_ce_detect_bands(h, t_d, m_d, b_d, nb, offs, p_d, q_d, cfg, k,
+                                  significance=False, stream=stream)
+        else:
+            g.gce_ce_topk(h, t_d, m_d, offs, p_d, q_d, cfg, k, out_H, out_I, stream=stream)
 
     tuned = {}
 
@@ -345,22 +357,37 @@ def main():
     hH = torch.empty((batch.n_curves, k), dtype=torch.float32).pin_memory()
     hI = torch.empty((batch.n_curves, k), dtype=torch.int64).pin_memory()
     cfg = g.Config(batch.n_phase, batch.n_mag, args.mode, t0=batch.t0)
+    hb = pin(bands_h) if nb else None
+
+    def e2e_step():
+        if not nb:
+            g.gce_ce_topk_host(h, ht, hm, offs, hp, hq, cfg, k, hH, hI, stream=stream)
+            return
+        # multi-filter input has no host-buffer entry point: the same copies, by hand
+        dt, dm, db, dp, dq = (x.to(dev, non_blocking=True) for x in (ht, hm, hb, hp, hq))
+        tH_, tI_, _, _, _ = g.gce_ce_detect_bands(h, dt, dm, db, nb, offs, dp, dq, cfg, k,
+                                                  significance=False, stream=stream)
+        hH.copy_(tH_, non_blocking=True)
+        hI.copy_(tI_, non_blocking=True)
+        stream.synchronize()
+
     with torch.cuda.stream(stream):
         for _ in range(max(1, args.warmup)):
-            g.gce_ce_topk_host(h, ht, hm, offs, hp, hq, cfg, k, hH, hI, stream=stream)
+            e2e_step()
         barrier()
         e2e_t = 0.0
         for _ in range(args.steps):
             flush.zero_()
             stream.synchronize()
             t0 = time.perf_counter()
-            g.gce_ce_topk_host(h, ht, hm, offs, hp, hq, cfg, k, hH, hI, stream=stream)
+            e2e_step()
             e2e_t += time.perf_counter() - t0
     if pg is not None:
         tt = torch.tensor([e2e_t], device=dev, dtype=torch.float64)
         pg.all_reduce(tt, op=pg.ReduceOp.MAX)
         e2e_t = float(tt.item())
-    h2d = 8 * (batch.times.size + batch.mags.size + batch.periods.size + batch.pdots.size)
+    h2d = 8 * (batch.times.size + batch.mags.size + batch.periods.size + batch.pdots.size) + (
+        batch.times.size if nb else 0)
     d2h = (4 + 8) * batch.n_curves * k
 
     extras = {}
@@ -448,10 +475,12 @@ def main():
                        "phase_mode": args.mode, "point_trials_per_step": pt_step,
                        "launch_shape": tuned.get(args.mode),
                        "l2": "256 MB buffer written between timed steps",
-                       "parallelism": f"replica per GPU x{world}"},
+                       "parallelism": f"replica per GPU x{world}",
+                       **({"filters": f"{nb} (seeded filter index per point; per-filter "
+                                      "median/std normalisation)"} if nb else {})},
             "e2e": {"value": pt_step * args.steps * world / e2e_t, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": 6 * args.steps,
+            "gpu_launches": (7 if nb else 6) * args.steps,
             "clocks": clocks,
             "roofline": roof,
             "cpu_baseline": cpu,
