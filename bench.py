@@ -68,6 +68,10 @@ def parse():
                     help="total oracle seconds of the reference arm (spread over its steps)")
     ap.add_argument("--curves", type=int, default=0,
                     help="use only the first N curves of the workload (profiling runs)")
+    ap.add_argument("--phase-bins", type=int, default=0,
+                    help="override the workload's phase-bin count (0 = the workload's)")
+    ap.add_argument("--overlap", action="store_true",
+                    help="50%%-overlapping phase bins (the paper's 50-bin production setting)")
     ap.add_argument("--bands", type=int, default=0,
                     help="multi-filter input: give every point one of N filters (seeded) and "
                          "search through gce_ce_detect_bands (0 = single filter)")
@@ -272,6 +276,9 @@ def main():
                                       batch.n_phase, batch.n_mag, glob.truth_p0[mine],
                                       glob.truth_pdot[mine], glob.truth_class[mine], batch.t0,
                                       batch.topk)
+    if args.phase_bins:
+        batch.n_phase = int(args.phase_bins)
+    ovl = bool(args.overlap)
     k = batch.topk or 5
     pt_step = batch.point_trials
     t_d = torch.tensor(batch.times, device=dev)
@@ -291,7 +298,8 @@ def main():
     b_d = torch.tensor(bands_h, device=dev) if nb else None
 
     def step(mode, time_kernel=False):
-        cfg = g.Config(batch.n_phase, batch.n_mag, mode, t0=batch.t0, time_kernel=time_kernel)
+        cfg = g.Config(batch.n_phase, batch.n_mag, mode, t0=batch.t0, time_kernel=time_kernel,
+                       overlap=ovl)
         if nb:
             g.gce_ce_detect_bands(h, t_d, m_d, b_d, nb, offs, p_d, q_d, cfg, k,
                                   significance=False, stream=stream)
@@ -302,13 +310,12 @@ def main():
 
     def timed_steps(mode, warmup, steps, with_kernel=False):
         if mode not in tuned:  # launch-shape autotuning is part of the untimed warm-up
-            cfg = g.Config(batch.n_phase, batch.n_mag, mode, t0=batch.t0)
+            cfg = g.Config(batch.n_phase, batch.n_mag, mode, t0=batch.t0, overlap=ovl)
             if args.shape:
                 b_, t_, c_ = (int(x) for x in args.shape.split(","))
                 g.gce_set_tuning(h, cfg, int(batch.n_obs.max()), block=b_, tpt=t_, chunk=c_)
-            else:
-                g.gce_autotune(h, cfg, int(batch.n_obs.max()),
-                               batch.periods.size * batch.pdots.size)
+            else:  # tuned on a bounded slice of this very job
+                g.gce_autotune_job(h, t_d, m_d, offs, p_d, q_d, cfg)
             tuned[mode] = g.gce_get_tuning(h, cfg, int(batch.n_obs.max()), int(batch.pdots.size))
         with torch.cuda.stream(stream):
             for _ in range(warmup):
@@ -356,7 +363,7 @@ def main():
     ht, hm, hp, hq = pin(batch.times), pin(batch.mags), pin(batch.periods), pin(batch.pdots)
     hH = torch.empty((batch.n_curves, k), dtype=torch.float32).pin_memory()
     hI = torch.empty((batch.n_curves, k), dtype=torch.int64).pin_memory()
-    cfg = g.Config(batch.n_phase, batch.n_mag, args.mode, t0=batch.t0)
+    cfg = g.Config(batch.n_phase, batch.n_mag, args.mode, t0=batch.t0, overlap=ovl)
     hb = pin(bands_h) if nb else None
 
     def e2e_step():
@@ -408,7 +415,8 @@ def main():
         if pt_step / 6e10 > 60.0 or grid_bytes > 8e9:
             extras["fp64_single_launch"] = {"skipped": "one step would take more than a minute"}
         else:
-            cfg64 = g.Config(batch.n_phase, batch.n_mag, "fp64", t0=batch.t0, time_kernel=True)
+            cfg64 = g.Config(batch.n_phase, batch.n_mag, "fp64", t0=batch.t0, time_kernel=True,
+                             overlap=ovl)
             with torch.cuda.stream(stream):
                 out = torch.empty((batch.n_curves, batch.pdots.size, batch.periods.size),
                                   dtype=torch.float32, device=dev)
@@ -477,7 +485,8 @@ def main():
                        "l2": "256 MB buffer written between timed steps",
                        "parallelism": f"replica per GPU x{world}",
                        **({"filters": f"{nb} (seeded filter index per point; per-filter "
-                                      "median/std normalisation)"} if nb else {})},
+                                      "median/std normalisation)"} if nb else {}),
+                       **({"phase_bins": "50 % overlapping"} if ovl else {})},
             "e2e": {"value": pt_step * args.steps * world / e2e_t, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": (7 if nb else 6) * args.steps,

@@ -272,6 +272,18 @@ gce_status gce_kernel_time(gce_handle h, float *ms);
 gce_status gce_autotune(gce_handle h, const gce_config *cfg, int32_t n_obs_hint,
                         int64_t n_trials_hint);
 
+/* Tune on the caller's own job (arguments as gce_ce_grid, without the output):
+ * the candidate shapes are timed on a bounded slice of it -- a prefix of the
+ * curves holding about 4e9 point-trials of the slice, at most 65536 periods and
+ * 8 Pdot values, each a strided subset spanning the job's range -- and the
+ * fastest is cached under the job's key (phase mode, bins, length bucket of
+ * its longest curve, Pdot axis or not), which later calls on that job use.
+ * Synchronous; it allocates and frees a small scratch of its own. */
+gce_status gce_autotune_job(gce_handle h, const double *times, const double *mags,
+                            const int64_t *h_offsets, int32_t n_curves, const double *periods,
+                            int32_t n_periods, const double *pdots, int32_t n_pdots,
+                            const gce_config *cfg);
+
 /* Read the launch shape the handle would use for a job with this config,
  * typical curve length and number of Pdot values (n_pdots_hint >= 1; > 1 means
  * a Pdot axis), or force one (gce_set_tuning replaces the cached choice for

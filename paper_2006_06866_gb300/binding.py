@@ -74,6 +74,7 @@ SIGNATURES = {
     "gce_stream_status": (_I32, [_P, _P]),
     "gce_kernel_time": (_I32, [_P, ctypes.POINTER(ctypes.c_float)]),
     "gce_autotune": (_I32, [_P, _CFG, _I32, _I64]),
+    "gce_autotune_job": (_I32, [_P, _P, _P, _HOFF, _I32, _P, _I32, _P, _I32, _CFG]),
     "gce_get_tuning": (_I32, [_P, _CFG, _I32, _I32, _TUN]),
     "gce_set_tuning": (_I32, [_P, _CFG, _I32, _TUN]),
 }
@@ -395,6 +396,14 @@ def gce_autotune(handle: Handle, cfg: Config, n_obs_hint: int, n_trials_hint: in
     c = cfg.c()
     _check(lib().gce_autotune(handle.ptr, ctypes.byref(c), int(n_obs_hint), int(n_trials_hint)),
            handle.ptr)
+
+
+def gce_autotune_job(handle: Handle, times, mags, offsets, periods, pdots, cfg: Config):
+    """Tune the launch shape on a bounded slice of this job (see gce.h)."""
+    off, poff, pt, pm, pp, pd = _common(times, mags, offsets, periods, pdots)
+    c = cfg.c()
+    _check(lib().gce_autotune_job(handle.ptr, pt, pm, poff, off.shape[0] - 1, pp, periods.numel(),
+                                  pd, pdots.numel(), ctypes.byref(c)), handle.ptr)
 
 
 def gce_get_tuning(handle: Handle, cfg: Config, n_obs_hint: int, n_pdots: int = 1):

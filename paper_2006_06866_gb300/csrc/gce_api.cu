@@ -310,10 +310,28 @@ gce_status make_plan(gce_handle h, const Job &j, Plan &pl) {
     pl.pd_major = tg.pd_major;
     pl.n_items = (long long)j.n_curves * pl.n_tiles;
     CUDA_TRY(h, main_kernel_attrs(cfg->phase_mode, pl.tpt, pl.block, pl.smem));
+    const void *kern = main_kernel_ptr(cfg->phase_mode, pl.tpt, pl.block);
     int occ = 0;
-    CUDA_TRY(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                    &occ, main_kernel_ptr(cfg->phase_mode, pl.tpt, pl.block), pl.block, pl.smem));
+    CUDA_TRY(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, pl.block, pl.smem));
     if (occ < 1) return fail(h, GCE_ERR_UNSUPPORTED, "launch shape does not fit on an SM");
+    // A smaller staged chunk costs only more staging passes: take it whenever it
+    // admits more CTAs per SM (the counters leave little room at many phase bins,
+    // and the top-k buffer grows with k, so the tuned chunk can sit just past an
+    // occupancy step for another k).
+    while (pl.chunk > 256) {
+        const int keep = pl.chunk;
+        pl.chunk = std::max(256, (pl.chunk / 2 + 31) / 32 * 32);
+        const size_t sm2 = size();
+        int occ2 = 0;
+        CUDA_TRY(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, kern, pl.block, sm2));
+        if (occ2 > occ) {
+            pl.smem = sm2;
+            occ = occ2;
+        } else {
+            pl.chunk = keep;
+            break;
+        }
+    }
     if (t.ctas_per_sm > 0) occ = std::min(occ, t.ctas_per_sm);
     long long g = (long long)h->n_sm * occ;
     g = std::min(g, std::max(pl.n_items, 1ll));
@@ -749,6 +767,114 @@ extern "C" gce_status gce_set_tuning(gce_handle h, const gce_config *cfg, int32_
     return GCE_OK;
 }
 
+// Candidate launch shapes of the autotuners.
+static std::vector<gce_tuning> tune_candidates(int mode, int n_obs) {
+    const int blocks[] = {128, 256, 512};
+    const int tpts[] = {1, 2, 4};
+    const int chunks[] = {256, 512, 1024, 2048};
+    std::vector<gce_tuning> cands;
+    for (int b : blocks)
+        for (int tp : tpts)
+            for (int ch : chunks) {
+                if (ch > 512 && ch >= 2 * n_obs) continue;  // same plan as a smaller chunk
+                if (tp == 4 && mode == GCE_PHASE_FP64) continue;  // not built
+                gce_tuning c = default_tuning(mode, n_obs);
+                c.block = b;
+                c.tpt = tp;
+                c.chunk = ch;
+                cands.push_back(c);
+            }
+    return cands;
+}
+
+// Times every candidate on job j (one untimed run, then three timed ones) and
+// leaves the fastest in *best; shapes that do not fit are skipped.
+static gce_status time_candidates(gce_handle h, Job j, const std::vector<gce_tuning> &cands,
+                                  cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1,
+                                  gce_tuning *best) {
+    float best_ms = 1e30f;
+    for (const gce_tuning &cand : cands) {
+        j.force = &cand;
+        if (run_job(h, j, s) != GCE_OK) continue;
+        cudaEventRecord(e0, s);
+        for (int rep = 0; rep < 3; ++rep) run_job(h, j, s);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess)
+            return fail(h, GCE_ERR_CUDA, "autotune: %s", cudaGetErrorString(cudaGetLastError()));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+            best_ms = ms;
+            *best = cand;
+        }
+    }
+    return GCE_OK;
+}
+
+extern "C" gce_status gce_autotune_job(gce_handle h, const double *times, const double *mags,
+                                       const int64_t *h_offsets, int32_t n_curves,
+                                       const double *periods, int32_t n_periods,
+                                       const double *pdots, int32_t n_pdots,
+                                       const gce_config *cfg) {
+    if (!h || !cfg) return GCE_ERR_INVALID;
+    const gce_status chk = gce_check_job(h_offsets, n_curves, n_periods, n_pdots, cfg, 0);
+    if (chk != GCE_OK) return fail(h, chk, "autotune: argument check failed");
+    if (n_curves == 0) return GCE_OK;
+    if (!times || !mags || !periods || !pdots) return fail(h, GCE_ERR_INVALID, "NULL input array");
+    CUDA_TRY(h, cudaSetDevice(h->device));
+    // the slice: up to 65536 periods and 8 Pdot values, each a strided subset that
+    // spans the job's range, and a prefix of the curves with about 4e9 point-trials
+    const int p_s = n_periods > 65536 ? (n_periods + 65535) / 65536 : 1;
+    const int n_p2 = (n_periods + p_s - 1) / p_s;
+    const int q_s = n_pdots > 8 ? (n_pdots + 7) / 8 : 1;
+    const int n_q2 = (n_pdots + q_s - 1) / q_s;
+    const long long trials = (long long)n_p2 * n_q2;
+    int c2 = 0;
+    long long pts = 0, nmax = 1;
+    for (int c = 0; c < n_curves; ++c) nmax = std::max<long long>(nmax, h_offsets[c + 1] - h_offsets[c]);
+    while (c2 < n_curves && pts * trials < 4000000000ll) {
+        pts += h_offsets[c2 + 1] - h_offsets[c2];
+        ++c2;
+    }
+    double *d_p = nullptr, *d_q = nullptr;
+    float *d_H = nullptr;
+    int64_t *d_I = nullptr;
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    gce_status result = GCE_OK;
+    gce_tuning best = default_tuning(cfg->phase_mode, (int)nmax);
+    gce_config c2cfg = *cfg;
+    c2cfg.flags = (c2cfg.flags | GCE_FLAG_NO_GRAPH) & ~GCE_FLAG_TIME_KERNEL;
+    do {
+        if (cudaMalloc(&d_p, 8 * (size_t)n_p2) || cudaMalloc(&d_q, 8 * (size_t)n_q2) ||
+            cudaMalloc(&d_H, 4 * (size_t)c2) || cudaMalloc(&d_I, 8 * (size_t)c2) ||
+            cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) || cudaEventCreate(&e0) ||
+            cudaEventCreate(&e1)) {
+            result = fail(h, GCE_ERR_NOMEM, "autotune: allocation failed");
+            break;
+        }
+        // strided copies: one element every p_s (q_s) of the caller's arrays
+        if (cudaMemcpy2DAsync(d_p, 8, periods, 8 * (size_t)p_s, 8, n_p2, cudaMemcpyDeviceToDevice, s) ||
+            cudaMemcpy2DAsync(d_q, 8, pdots, 8 * (size_t)q_s, 8, n_q2, cudaMemcpyDeviceToDevice, s)) {
+            result = fail(h, GCE_ERR_CUDA, "autotune: %s", cudaGetErrorString(cudaGetLastError()));
+            break;
+        }
+        Job j{};
+        j.kind = JOB_TOPK;
+        j.times = times; j.mags = mags; j.h_offsets = h_offsets; j.n_curves = c2;
+        j.periods = d_p; j.n_periods = n_p2; j.pdots = d_q; j.n_pdots = n_q2;
+        j.cfg = &c2cfg; j.k = 1; j.topk_H = d_H; j.topk_idx = d_I;
+        result = time_candidates(h, j, tune_candidates(cfg->phase_mode, (int)nmax), s, e0, e1, &best);
+    } while (0);
+    if (s) cudaStreamSynchronize(s);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (s) cudaStreamDestroy(s);
+    cudaFree(d_p); cudaFree(d_q); cudaFree(d_H); cudaFree(d_I);
+    if (result == GCE_OK) h->tune[tune_key(cfg, (int)nmax, n_pdots > 1 ? 1 : 0)] = best;
+    return result;
+}
+
 extern "C" gce_status gce_autotune(gce_handle h, const gce_config *cfg, int32_t n_obs_hint,
                                    int64_t n_trials_hint) {
     if (!h || !cfg) return GCE_ERR_INVALID;
@@ -788,9 +914,6 @@ extern "C" gce_status gce_autotune(gce_handle h, const gce_config *cfg, int32_t 
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     gce_status result = GCE_OK;
     gce_tuning best[2] = {default_tuning(cfg->phase_mode, n_obs), default_tuning(cfg->phase_mode, n_obs)};
-    const int blocks[] = {128, 256, 512};
-    const int tpts[] = {1, 2, 4};
-    const int chunks[] = {256, 512, 1024, 2048};
     gce_config c2 = *cfg;
     c2.flags |= GCE_FLAG_NO_GRAPH;
     do {
@@ -807,46 +930,19 @@ extern "C" gce_status gce_autotune(gce_handle h, const gce_config *cfg, int32_t 
         cudaMemcpy(d_p, per.data(), 8 * n_tr, cudaMemcpyHostToDevice);
         cudaMemcpy(d_pp, perp.data(), 8 * n_trp, cudaMemcpyHostToDevice);
         cudaMemcpy(d_d, pd.data(), 8 * n_pd, cudaMemcpyHostToDevice);
-        std::vector<gce_tuning> cands;
-        for (int b : blocks)
-            for (int tp : tpts)
-                for (int ch : chunks) {
-                    if (ch > 512 && ch >= 2 * n_obs) continue;  // same plan as a smaller chunk
-                    if (tp == 4 && cfg->phase_mode == GCE_PHASE_FP64) continue;  // not built
-                    gce_tuning c = default_tuning(cfg->phase_mode, n_obs);
-                    c.block = b;
-                    c.tpt = tp;
-                    c.chunk = ch;
-                    cands.push_back(c);
-                }
+        const std::vector<gce_tuning> cands = tune_candidates(cfg->phase_mode, n_obs);
         // pass 0: one Pdot value (pd[0] = 0); pass 1: the Pdot axis
         for (int pass = 0; pass < 2 && result == GCE_OK; ++pass) {
-            float best_ms = 1e30f;
-            for (const gce_tuning &cand : cands) {
-                Job j{};
-                j.kind = JOB_GRID;
-                j.times = d_t; j.mags = d_m; j.h_offsets = offs; j.n_curves = n_curves;
-                if (pass == 0) {
-                    j.periods = d_p; j.n_periods = (int)n_tr; j.pdots = d_d; j.n_pdots = 1;
-                } else {
-                    j.periods = d_pp; j.n_periods = (int)n_trp; j.pdots = d_d; j.n_pdots = n_pd;
-                }
-                j.cfg = &c2; j.out = d_out; j.force = &cand;
-                if (run_job(h, j, s) != GCE_OK) continue;  // shape does not fit: skip it
-                cudaEventRecord(e0, s);
-                for (int rep = 0; rep < 3; ++rep) run_job(h, j, s);
-                cudaEventRecord(e1, s);
-                if (cudaEventSynchronize(e1) != cudaSuccess) {
-                    result = fail(h, GCE_ERR_CUDA, "autotune: %s", cudaGetErrorString(cudaGetLastError()));
-                    break;
-                }
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (ms < best_ms) {
-                    best_ms = ms;
-                    best[pass] = cand;
-                }
+            Job j{};
+            j.kind = JOB_GRID;
+            j.times = d_t; j.mags = d_m; j.h_offsets = offs; j.n_curves = n_curves;
+            if (pass == 0) {
+                j.periods = d_p; j.n_periods = (int)n_tr; j.pdots = d_d; j.n_pdots = 1;
+            } else {
+                j.periods = d_pp; j.n_periods = (int)n_trp; j.pdots = d_d; j.n_pdots = n_pd;
             }
+            j.cfg = &c2; j.out = d_out;
+            result = time_candidates(h, j, cands, s, e0, e1, &best[pass]);
         }
     } while (0);
     if (s) cudaStreamSynchronize(s);

@@ -271,9 +271,9 @@ __device__ __forceinline__ unsigned int fold_fixed_bin_from(unsigned int acc, ui
 
 // ------------------------------------------------------------------ entropy
 
-// The counter slots a trial keeps: logical slots [zmin, zmax] (plus logical
-// -1 below them with overlapping bins).  FP64 and FIXED32 count phase bins
-// directly.  SPLIT32's slot is floor(x n + n) for the fold residual x; a job
+// The counter slots a trial keeps: logical slots [zmin, zmax] (fine phase
+// bins; 50 %-overlapping bins are formed from them in the epilogue).  FP64 and
+// FIXED32 count phase bins directly.  SPLIT32's slot is floor(x n + n) for the fold residual x; a job
 // that passes the range check (cycles < 2^21) has |x| <= 3/4 + 2^-20 (r within
 // 1/2, each cross term within 2^-24 |th fh| < 1/8, three roundings), so slots
 // outside [floor(n (1/4 - 2^-16)), floor(n (7/4 + 2^-16))] are never reached.
@@ -289,9 +289,9 @@ __host__ __device__ inline SlotRange slot_range(int mode, int n_phase) {
     if (zmax > 2 * n_phase - 1) zmax = 2 * n_phase - 1;
     return {zmin, zmax};
 }
-__host__ __device__ inline int slots_per_trial(int mode, int n_phase, int overlap) {
+__host__ __device__ inline int slots_per_trial(int mode, int n_phase) {
     const SlotRange r = slot_range(mode, n_phase);
-    return r.zmax - r.zmin + 1 + (overlap ? 1 : 0);
+    return r.zmax - r.zmin + 1;
 }
 
 // Fixed-point table of c ln c: tab[c] = round(c ln(c) 2^32), tab[0] = tab[1] = 0.

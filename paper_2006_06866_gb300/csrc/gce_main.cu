@@ -182,11 +182,11 @@ __device__ __forceinline__ void compiler_fence() { asm volatile("" ::: "memory")
 // the thread's TPT trials and counted into the thread's private counters.
 // base[s]: shared-memory address of trial s's logical slot 0 minus the mode's
 // slot bias (mod 2^32); a slot's word is base + (raw << SH), SH = log2(4 block).
-// With OVL (50 %-overlapping phase bins, Sec. 2.3) each point also counts in
-// the bin below, the word one slot stride lower (logical slot -1 exists).
+// Each point counts once, in its fine phase bin, also with 50 %-overlapping
+// bins (their counts are sums of adjacent fine bins, formed in the epilogue).
 // SHARED: the thread's trials share their period (period-major tiles), so the
 // fold's period part is computed once per point for all of them.
-template <int MODE, int TPT, int SH, bool PDOT, bool K0, bool OVL, bool SHARED>
+template <int MODE, int TPT, int SH, bool PDOT, bool K0, bool SHARED>
 __device__ __forceinline__ void count_points(
     const typename ModeTraits<MODE>::point_t *__restrict__ pts, int ka, int kb,
     const typename Fold<MODE>::prep_t (&tc)[TPT], const unsigned int (&base)[TPT],
@@ -202,24 +202,18 @@ __device__ __forceinline__ void count_points(
                 base[s] + (SHARED ? Fold<MODE>::template offset_from<PDOT, K0, SH>(fp, p, tc[s], fk)
                                   : Fold<MODE>::template offset<PDOT, K0, SH>(p, tc[s], fk));
             red_shared_inc(addr);
-            if (OVL) red_shared_inc(addr - (1u << SH));
         }
     }
 }
 
 template <int MODE, int TPT, int SH, bool PDOT, bool K0>
-__device__ __forceinline__ void count_points_ovl(
-    bool ovl, bool shared, const typename ModeTraits<MODE>::point_t *__restrict__ pts, int ka,
-    int kb, const typename Fold<MODE>::prep_t (&tc)[TPT], const unsigned int (&base)[TPT],
+__device__ __forceinline__ void count_points_any(
+    bool shared, const typename ModeTraits<MODE>::point_t *__restrict__ pts, int ka, int kb,
+    const typename Fold<MODE>::prep_t (&tc)[TPT], const unsigned int (&base)[TPT],
     const FoldConst &fk) {
     constexpr bool SH_OK = PDOT && TPT > 1;  // sharing pays only with a Pdot term
-    if (SH_OK && shared) {
-        if (ovl) count_points<MODE, TPT, SH, PDOT, K0, true, SH_OK>(pts, ka, kb, tc, base, fk);
-        else count_points<MODE, TPT, SH, PDOT, K0, false, SH_OK>(pts, ka, kb, tc, base, fk);
-    } else {
-        if (ovl) count_points<MODE, TPT, SH, PDOT, K0, true, false>(pts, ka, kb, tc, base, fk);
-        else count_points<MODE, TPT, SH, PDOT, K0, false, false>(pts, ka, kb, tc, base, fk);
-    }
+    if (SH_OK && shared) count_points<MODE, TPT, SH, PDOT, K0, SH_OK>(pts, ka, kb, tc, base, fk);
+    else count_points<MODE, TPT, SH, PDOT, K0, false>(pts, ka, kb, tc, base, fk);
 }
 
 // c_ij of one phase bin at the end of a magnitude segment (low - snapshot), with
@@ -234,15 +228,17 @@ __device__ __forceinline__ int take_segment(unsigned int *w) {
 
 // For each of the thread's TPT trials, sum_j T(c_j) over the phase bins, where
 // bin j's count is spread over the logical slots l in [L, R] with l = j (mod
-// n_phase): l, l + n_phase and, only in a window 2 n_phase + 1 slots wide
-// (overlap with every slot live), l + 2 n_phase.  Trial s's slot l is the word
-// wb[s] + (l + off) stride_j (logical -1 exists with overlapping bins).  SEG: the
-// counts since the last segment end, each slot's snapshot moved up to its
-// count (take_segment's update); else the cumulative counts.  Slot values stay
-// shifted left by 16 until the lookup, so a bin's slots add without a shift.
-// Each step loads the counters of a few bins of every trial before it stores
-// any, so the loads overlap instead of waiting on the previous stores.
-template <int TPT, bool SEG, bool ALL_SMEM>
+// n_phase): l, l + n_phase and, only in a window 2 n_phase wide or more,
+// l + 2 n_phase.  Trial s's slot l is the word wb[s] + (l + off) stride_j.
+// SEG: the counts since the last segment end, each slot's snapshot moved up to
+// its count (take_segment's update); else the cumulative counts.  Slot values
+// stay shifted left by 16 until the lookup, so a bin's slots add without a
+// shift.  OVL (50 %-overlapping bins, Sec. 2.3): overlapping bin j holds the
+// fine bins j and j + 1, so the sum is over T(c_j + c_{j+1}) of consecutive fine
+// bins (the bins are visited in cyclic order), closed by the last and the
+// first.  Each step loads the counters of a few bins of every trial before it
+// stores any, so the loads overlap instead of waiting on the previous stores.
+template <int TPT, bool SEG, bool ALL_SMEM, bool OVL>
 struct BinWindow {
     unsigned int *const (&wb)[TPT];
     const int off;  // physical slot of logical slot 0
@@ -250,10 +246,13 @@ struct BinWindow {
     const unsigned long long *s_tab;
     const int table_smem;
     const unsigned long long *g_tab;
+    // OVL: the first and the previous fine bin's count (shifted left by 16)
+    unsigned int first[TPT] = {}, prev[TPT] = {};
+    bool started = false;
 
     // G bins starting at first slot l, each with C slots (l, l + n, l + 2n)
     template <int G, int C>
-    __device__ __forceinline__ void step(int l, int n, unsigned long long (&acc)[TPT]) const {
+    __device__ __forceinline__ void step(int l, int n, unsigned long long (&acc)[TPT]) {
         unsigned int *p[TPT][G][C];
         unsigned int v[TPT][G][C];
 #pragma unroll
@@ -274,8 +273,19 @@ struct BinWindow {
 #pragma unroll
                 for (int k = 0; k < C; ++k)
                     d += SEG ? __byte_perm(v[s][g][k], 0u, 0x1010) - v[s][g][k] : v[s][g][k] << 16;
-                t[s][g] = tab_lookup<ALL_SMEM>(s_tab, table_smem, g_tab, (int)(d >> 16));
+                if (OVL) {
+                    if (g == 0 && !started) {  // the first fine bin: kept for the closing pair
+                        first[s] = d;
+                        t[s][g] = 0ull;
+                    } else {
+                        t[s][g] = tab_lookup<ALL_SMEM>(s_tab, table_smem, g_tab, (int)((prev[s] + d) >> 16));
+                    }
+                    prev[s] = d;
+                } else {
+                    t[s][g] = tab_lookup<ALL_SMEM>(s_tab, table_smem, g_tab, (int)(d >> 16));
+                }
             }
+        if (OVL) started = true;
         if (SEG) {
 #pragma unroll
             for (int s = 0; s < TPT; ++s)
@@ -290,7 +300,7 @@ struct BinWindow {
             for (int g = 0; g < G; ++g) acc[s] += t[s][g];
     }
 
-    __device__ __forceinline__ void sum(int n, int L, int R, unsigned long long (&acc)[TPT]) const {
+    __device__ __forceinline__ void sum(int n, int L, int R, unsigned long long (&acc)[TPT]) {
         const int last = L + n - 1;  // every bin's first slot lies in [L, last]
         int l = L;
         if (R - L >= 2 * n) {
@@ -304,6 +314,11 @@ struct BinWindow {
         for (; l <= pe; ++l) step<1, 2>(l, n, acc);
         for (; l + GS - 1 <= last; l += GS) step<GS, 1>(l, n, acc);
         for (; l <= last; ++l) step<1, 1>(l, n, acc);
+        if (OVL) {
+#pragma unroll
+            for (int s = 0; s < TPT; ++s)
+                acc[s] += tab_lookup<ALL_SMEM>(s_tab, table_smem, g_tab, (int)((prev[s] + first[s]) >> 16));
+        }
     }
 };
 
@@ -344,20 +359,20 @@ __device__ __forceinline__ void chan_merge(double &n, double &mean, double &m2, 
 }
 
 // CTAs per SM the register allocation is sized for.  With two trials per
-// thread the FP32 folds' counters already limit shared memory to about three
-// 256-thread CTAs per SM at 15 phase bins, so those kernels take the registers
-// that frees (80 at 256 threads) instead of 64.
+// thread the counters (and FP64's wider staged points) already limit shared
+// memory to about three 256-thread CTAs per SM at 15 phase bins, so those
+// kernels take the registers that frees (80 at 256 threads) instead of 64.
 // Four trials per thread need four times the counters of one: at most 512
 // threads per SM fit, and those kernels take up to 128 registers.
-constexpr int main_min_blocks(int mode, int tpt, int log2b) {
+constexpr int main_min_blocks(int tpt, int log2b) {
     return tpt == 4 ? (log2b >= 9 ? 1 : (log2b == 8 ? 2 : (log2b == 7 ? 4 : 8)))
-           : tpt == 2 && mode != GCE_PHASE_FP64
+           : tpt == 2
                ? (log2b >= 9 ? 2 : (log2b == 8 ? 3 : (log2b == 7 ? 6 : 8)))
                : (log2b >= 9 ? 2 : (log2b == 8 ? 4 : 8));
 }
 
 template <int MODE, int TPT, int LOG2B>
-__global__ void __launch_bounds__(1 << LOG2B, main_min_blocks(MODE, TPT, LOG2B)) k_main(MainArgs a) {
+__global__ void __launch_bounds__(1 << LOG2B, main_min_blocks(TPT, LOG2B)) k_main(MainArgs a) {
     typedef typename ModeTraits<MODE>::point_t point_t;
     typedef typename ModeTraits<MODE>::trial_t trial_t;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -372,8 +387,8 @@ __global__ void __launch_bounds__(1 << LOG2B, main_min_blocks(MODE, TPT, LOG2B))
     constexpr bool SPLIT = MODE == GCE_PHASE_SPLIT32;
     const int ovl = a.overlap ? 1 : 0;
     const SlotRange zr = slot_range(MODE, n_phase);
-    const int n_slots = slots_per_trial(MODE, n_phase, ovl);
-    const int slot_off = ovl - zr.zmin;  // physical index of logical slot l: l + slot_off
+    const int n_slots = slots_per_trial(MODE, n_phase);
+    const int slot_off = -zr.zmin;  // physical index of logical slot l: l + slot_off
     const int stride_j = B, stride_s = n_slots * B;
 
     point_t *s_pts = reinterpret_cast<point_t *>(smem);
@@ -457,7 +472,7 @@ __global__ void __launch_bounds__(1 << LOG2B, main_min_blocks(MODE, TPT, LOG2B))
         const bool pdot = __syncthreads_or(any_pdot) != 0;
         const bool k0 = MODE != GCE_PHASE_FIXED32 || __syncthreads_and(all_k0) != 0;
         // live logical slots [L, R] of this warp's counters (warp-uniform)
-        int L = -ovl, R = n_phase - 1;
+        int L = 0, R = n_phase - 1;
         if (SPLIT) {
             float fm = 0.0f;
 #pragma unroll
@@ -466,7 +481,7 @@ __global__ void __launch_bounds__(1 << LOG2B, main_min_blocks(MODE, TPT, LOG2B))
             fm = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(fm)));
             int zlo, zhi;
             split_slot_window(pdot, tau_max_f * fm, n_phase, zlo, zhi);
-            L = max(zlo, zr.zmin) - ovl;
+            L = max(zlo, zr.zmin);
             R = min(zhi, zr.zmax);
         }
 
@@ -490,24 +505,32 @@ __global__ void __launch_bounds__(1 << LOG2B, main_min_blocks(MODE, TPT, LOG2B))
                 if (ka < kb) {
                     compiler_fence();
                     const typename ModeTraits<MODE>::point_t *pp = s_pts;
-                    const bool ov = ovl != 0;
                     if (k0) {
-                        if (pdot) count_points_ovl<MODE, TPT, SH, true, true>(ov, pdm, pp, ka - lo, kb - lo, tc, base, fk);
-                        else count_points_ovl<MODE, TPT, SH, false, true>(ov, pdm, pp, ka - lo, kb - lo, tc, base, fk);
+                        if (pdot) count_points_any<MODE, TPT, SH, true, true>(pdm, pp, ka - lo, kb - lo, tc, base, fk);
+                        else count_points_any<MODE, TPT, SH, false, true>(pdm, pp, ka - lo, kb - lo, tc, base, fk);
                     } else if (MODE == GCE_PHASE_FIXED32) {
-                        if (pdot) count_points_ovl<MODE, TPT, SH, true, false>(ov, pdm, pp, ka - lo, kb - lo, tc, base, fk);
-                        else count_points_ovl<MODE, TPT, SH, false, false>(ov, pdm, pp, ka - lo, kb - lo, tc, base, fk);
+                        if (pdot) count_points_any<MODE, TPT, SH, true, false>(pdm, pp, ka - lo, kb - lo, tc, base, fk);
+                        else count_points_any<MODE, TPT, SH, false, false>(pdm, pp, ka - lo, kb - lo, tc, base, fk);
                     }
                     compiler_fence();
                 }
                 if (s1 > s0 && s1 > lo && s1 <= hi) {
                     // end of magnitude segment i: c_ij = counter - snapshot
-                    if (tab_all)
-                        BinWindow<TPT, true, true>{wbase, slot_off, stride_j, s_tab, a.table_smem, a.table}
-                            .sum(n_phase, L, R, s_ij);
-                    else
-                        BinWindow<TPT, true, false>{wbase, slot_off, stride_j, s_tab, a.table_smem, a.table}
-                            .sum(n_phase, L, R, s_ij);
+                    if (ovl) {
+                        if (tab_all)
+                            BinWindow<TPT, true, true, true>{wbase, slot_off, stride_j, s_tab, a.table_smem, a.table}
+                                .sum(n_phase, L, R, s_ij);
+                        else
+                            BinWindow<TPT, true, false, true>{wbase, slot_off, stride_j, s_tab, a.table_smem, a.table}
+                                .sum(n_phase, L, R, s_ij);
+                    } else {
+                        if (tab_all)
+                            BinWindow<TPT, true, true, false>{wbase, slot_off, stride_j, s_tab, a.table_smem, a.table}
+                                .sum(n_phase, L, R, s_ij);
+                        else
+                            BinWindow<TPT, true, false, false>{wbase, slot_off, stride_j, s_tab, a.table_smem, a.table}
+                                .sum(n_phase, L, R, s_ij);
+                    }
                 }
             }
         }
@@ -519,7 +542,10 @@ __global__ void __launch_bounds__(1 << LOG2B, main_min_blocks(MODE, TPT, LOG2B))
         float hv[TPT];
 #pragma unroll
         for (int s = 0; s < TPT; ++s) sjs[s] = 0ull;
-        BinWindow<TPT, false, false>{wbase, slot_off, stride_j, s_tab, a.table_smem, a.table}.sum(n_phase, L, R, sjs);
+        if (ovl)
+            BinWindow<TPT, false, false, true>{wbase, slot_off, stride_j, s_tab, a.table_smem, a.table}.sum(n_phase, L, R, sjs);
+        else
+            BinWindow<TPT, false, false, false>{wbase, slot_off, stride_j, s_tab, a.table_smem, a.table}.sum(n_phase, L, R, sjs);
 #pragma unroll
         for (int s = 0; s < TPT; ++s) {
             const unsigned long long sj = sjs[s];
@@ -771,7 +797,7 @@ size_t main_smem_bytes(int mode, int block, int tpt, int chunk, int n_phase, int
                        int table_smem, int k, int overlap) {
     size_t pt = mode == GCE_PHASE_FP64 ? 8 : 16;
     size_t b = pt * (size_t)chunk + 8 * (size_t)table_smem +
-               4 * (size_t)tpt * slots_per_trial(mode, n_phase, overlap) * block +
+               4 * (size_t)tpt * slots_per_trial(mode, n_phase) * block +
                4 * (size_t)((n_mag + 2) & ~1) + 8 * (size_t)(block / 32) * (size_t)(k > 0 ? k : 1) +
                24 * (size_t)(block / 32);
     return b;

@@ -128,6 +128,21 @@ def test_split_fold_near_cycle_limit(h, overlap):
         compare_grid("split32", got.cpu().numpy().astype(np.float64), ref, dmin)
 
 
+@pytest.mark.parametrize("pdots", [(0.0,), (0.0, -1e-11, -2e-11)])
+def test_autotune_on_the_job(h, pdots):
+    """Tuning on a slice of the job itself caches a valid shape under the job's key
+    and leaves the results unchanged."""
+    b = small_batch(seed=10, n_curves=3, n_obs=400, n_periods=3000, pdots=pdots)
+    args = dev_args(b)
+    cfg = g.Config(15, 10, "split32")
+    before = g.gce_ce_grid(h, cfg=cfg, **args).cpu().numpy()
+    g.gce_autotune_job(h, cfg=cfg, **args)
+    t = g.gce_get_tuning(h, cfg, 400, n_pdots=len(pdots))
+    assert t["block"] in (128, 256, 512) and t["tpt"] in (1, 2, 4)
+    after = g.gce_ce_grid(h, cfg=cfg, **args).cpu().numpy()
+    assert np.array_equal(before, after)
+
+
 def test_four_trials_per_thread_not_built_for_fp64(h):
     with pytest.raises(g.GceError):
         g.gce_set_tuning(h, g.Config(15, 10, "fp64"), 500, block=128, tpt=4)
