@@ -265,7 +265,7 @@ struct Job {
 
 struct Plan {
     long long n_points, n_trials, n_items;
-    int n_max, n_tiles, n_ptiles, pd_major, block, tpt, grid, chunk, table_smem, grab;
+    int n_max, n_tiles, n_ptiles, pd_major, narrow, block, tpt, grid, chunk, table_smem, grab;
     size_t smem;
 };
 
@@ -285,12 +285,13 @@ gce_status make_plan(gce_handle h, const Job &j, Plan &pl) {
     // read counts above it from global memory
     pl.table_smem = std::min(pl.n_max + 1, 2048);
     const int kk = j.kind == JOB_TOPK ? j.k : 0;
+    // a Pdot axis: SPLIT32 keeps the narrow slot range (every fold re-reduced)
+    pl.narrow = (cfg->phase_mode == GCE_PHASE_SPLIT32 && j.n_pdots > 1) ? 1 : 0;
     // shrink the staged chunk, then the table, then trials per thread, then the
     // block, until the CTA fits in shared memory
     auto size = [&]() {
         return main_smem_bytes(cfg->phase_mode, pl.block, pl.tpt, pl.chunk, cfg->n_phase_bins,
-                               cfg->n_mag_bins, pl.table_smem, kk,
-                               (cfg->flags & GCE_FLAG_OVERLAP) ? 1 : 0);
+                               cfg->n_mag_bins, pl.table_smem, kk, pl.narrow);
     };
     pl.smem = size();
     while (pl.smem > (size_t)h->smem_optin) {
@@ -318,19 +319,25 @@ gce_status make_plan(gce_handle h, const Job &j, Plan &pl) {
     // admits more CTAs per SM (the counters leave little room at many phase bins,
     // and the top-k buffer grows with k, so the tuned chunk can sit just past an
     // occupancy step for another k).
-    while (pl.chunk > 256) {
-        const int keep = pl.chunk;
-        pl.chunk = std::max(256, (pl.chunk / 2 + 31) / 32 * 32);
-        const size_t sm2 = size();
-        int occ2 = 0;
-        CUDA_TRY(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, kern, pl.block, sm2));
-        if (occ2 > occ) {
-            pl.smem = sm2;
-            occ = occ2;
-        } else {
-            pl.chunk = keep;
-            break;
+    // Every halving down to 256 points is tried; the largest chunk that reaches
+    // the best occupancy is kept.
+    {
+        int best_chunk = pl.chunk;
+        size_t best_smem = pl.smem;
+        for (int c = pl.chunk; c > 256;) {
+            c = std::max(256, (c / 2 + 31) / 32 * 32);
+            pl.chunk = c;
+            const size_t sm2 = size();
+            int occ2 = 0;
+            CUDA_TRY(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, kern, pl.block, sm2));
+            if (occ2 > occ) {
+                occ = occ2;
+                best_chunk = c;
+                best_smem = sm2;
+            }
         }
+        pl.chunk = best_chunk;
+        pl.smem = best_smem;
     }
     if (t.ctas_per_sm > 0) occ = std::min(occ, t.ctas_per_sm);
     long long g = (long long)h->n_sm * occ;
@@ -398,6 +405,7 @@ gce_status enqueue(gce_handle h, const Job &j, const Plan &pl, cudaStream_t s, b
     ma.n_tiles = pl.n_tiles;
     ma.n_ptiles = pl.n_ptiles;
     ma.pd_major = pl.pd_major;
+    ma.narrow = pl.narrow;
     ma.n_items = pl.n_items;
     ma.grab = pl.grab;
     ma.n_phase = cfg->n_phase_bins;
@@ -787,25 +795,41 @@ static std::vector<gce_tuning> tune_candidates(int mode, int n_obs) {
     return cands;
 }
 
-// Times every candidate on job j (one untimed run, then three timed ones) and
-// leaves the fastest in *best; shapes that do not fit are skipped.
+// Times every candidate on job j (one untimed run, then three timed ones), then
+// times the three fastest again over six runs each and leaves the fastest of
+// those in *best (a second look keeps close calls from being decided by one
+// noisy measurement); shapes that do not fit are skipped.
 static gce_status time_candidates(gce_handle h, Job j, const std::vector<gce_tuning> &cands,
                                   cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1,
                                   gce_tuning *best) {
-    float best_ms = 1e30f;
-    for (const gce_tuning &cand : cands) {
+    auto timed = [&](const gce_tuning &cand, int reps, float *ms) -> gce_status {
         j.force = &cand;
-        if (run_job(h, j, s) != GCE_OK) continue;
+        *ms = 1e30f;
+        if (run_job(h, j, s) != GCE_OK) return GCE_OK;  // does not fit: stays 1e30
         cudaEventRecord(e0, s);
-        for (int rep = 0; rep < 3; ++rep) run_job(h, j, s);
+        for (int rep = 0; rep < reps; ++rep) run_job(h, j, s);
         cudaEventRecord(e1, s);
         if (cudaEventSynchronize(e1) != cudaSuccess)
             return fail(h, GCE_ERR_CUDA, "autotune: %s", cudaGetErrorString(cudaGetLastError()));
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
+        cudaEventElapsedTime(ms, e0, e1);
+        *ms /= (float)reps;
+        return GCE_OK;
+    };
+    std::vector<std::pair<float, size_t>> first;
+    for (size_t i = 0; i < cands.size(); ++i) {
+        float ms;
+        if (gce_status st = timed(cands[i], 3, &ms)) return st;
+        if (ms < 1e30f) first.emplace_back(ms, i);
+    }
+    if (first.empty()) return GCE_OK;
+    std::sort(first.begin(), first.end());
+    float best_ms = 1e30f;
+    for (size_t r = 0; r < std::min<size_t>(3, first.size()); ++r) {
+        float ms;
+        if (gce_status st = timed(cands[first[r].second], 6, &ms)) return st;
         if (ms < best_ms) {
             best_ms = ms;
-            *best = cand;
+            *best = cands[first[r].second];
         }
     }
     return GCE_OK;

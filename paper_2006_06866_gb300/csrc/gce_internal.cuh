@@ -152,11 +152,14 @@ __device__ __forceinline__ float fold_split_fpart(float4 pt, float4 tr) {
 }
 
 // The rest of the fold from the period part c: the Pdot term -a tau^2 reduced
-// the same way, the sum reduced once more, then the slot.
-template <bool PDOT>
+// the same way, the sum reduced once more, then the slot.  REDUCE (without
+// Pdot): the residual is reduced once more as well, to |x| <= 1/2, for jobs that
+// keep only the narrow slot range.
+template <bool PDOT, bool REDUCE = false>
 __device__ __forceinline__ int fold_split_from(float c, float4 pt, float4 tr, float nphi,
                                                float zoff) {
     float x = c;
+    if (!PDOT && REDUCE) x = __fsub_rn(c, __fsub_rn(__fadd_rn(c, kRound), kRound));
     if (PDOT) {
         const float t2h = pt.z, t2l = pt.w;
         const float nah = tr.z, nal = tr.w;  // -a split
@@ -273,24 +276,27 @@ __device__ __forceinline__ unsigned int fold_fixed_bin_from(unsigned int acc, ui
 
 // The counter slots a trial keeps: logical slots [zmin, zmax] (fine phase
 // bins; 50 %-overlapping bins are formed from them in the epilogue).  FP64 and
-// FIXED32 count phase bins directly.  SPLIT32's slot is floor(x n + n) for the fold residual x; a job
-// that passes the range check (cycles < 2^21) has |x| <= 3/4 + 2^-20 (r within
-// 1/2, each cross term within 2^-24 |th fh| < 1/8, three roundings), so slots
-// outside [floor(n (1/4 - 2^-16)), floor(n (7/4 + 2^-16))] are never reached.
+// FIXED32 count phase bins directly.  SPLIT32's slot is floor(x n + n) for the
+// fold residual x; a job that passes the range check (cycles < 2^21) has |x| <=
+// 3/4 + 2^-20 (r within 1/2, each cross term within 2^-24 |th fh| < 1/8, three
+// roundings), so slots outside [floor(n (1/4 - 2^-16)), floor(n (7/4 + 2^-16))]
+// are never reached.  narrow: every fold of the job re-reduces its residual to
+// |x| <= 1/2 (jobs with a Pdot axis, whose folds do that anyway), and only
+// [floor(n (1/2 - 2^-16)), floor(n (3/2 + 2^-16))] is kept.
 struct SlotRange {
     int zmin, zmax;
 };
-__host__ __device__ inline SlotRange slot_range(int mode, int n_phase) {
+__host__ __device__ inline SlotRange slot_range(int mode, int n_phase, bool narrow) {
     if (mode != GCE_PHASE_SPLIT32) return {0, n_phase - 1};
-    const double xw = 0.75 + 1.0 / 65536.0;
+    const double xw = (narrow ? 0.5 : 0.75) + 1.0 / 65536.0;
     int zmin = (int)floor((double)n_phase * (1.0 - xw));
     int zmax = (int)floor((double)n_phase * (1.0 + xw));
     if (zmin < 0) zmin = 0;
     if (zmax > 2 * n_phase - 1) zmax = 2 * n_phase - 1;
     return {zmin, zmax};
 }
-__host__ __device__ inline int slots_per_trial(int mode, int n_phase) {
-    const SlotRange r = slot_range(mode, n_phase);
+__host__ __device__ inline int slots_per_trial(int mode, int n_phase, bool narrow) {
+    const SlotRange r = slot_range(mode, n_phase, narrow);
     return r.zmax - r.zmin + 1;
 }
 
@@ -367,6 +373,7 @@ struct MainArgs {
     int n_tiles;               // trial tiles per curve
     int n_ptiles;              // period-major tiling: tiles along the periods
     int pd_major;              // tile = block periods x tpt Pdot values (else flat runs)
+    int narrow;                // SPLIT32: narrow slot range, every fold re-reduced
     long long n_items;         // n_curves * n_tiles
     int grab;                  // items taken per work-counter increment
     int n_phase;
@@ -393,7 +400,7 @@ cudaError_t launch_band_stats(const double *mags, const unsigned char *bands,
                               double2 *stats, JobState *st, cudaStream_t s);
 cudaError_t launch_table(unsigned long long *table, int n_max, cudaStream_t s);
 size_t main_smem_bytes(int mode, int block, int tpt, int chunk, int n_phase, int n_mag,
-                       int table_smem, int k, int overlap);
+                       int table_smem, int k, int narrow);
 size_t single_smem_bytes(int n_phase, int block);
 cudaError_t main_kernel_attrs(int mode, int tpt, int block, size_t smem);
 const void *main_kernel_ptr(int mode, int tpt, int block);

@@ -100,16 +100,16 @@ template <> struct Fold<GCE_PHASE_FP64> {
     __device__ __forceinline__ static fpart_t fpart(double p, const prep_t &t) {
         return fold_fp64_fpart(p, t.x);
     }
-    template <bool PDOT, bool K0, int SH>
+    template <bool PDOT, bool K0, int SH, bool RED>
     __device__ __forceinline__ static unsigned int offset_from(fpart_t f, double p,
                                                                const prep_t &t,
                                                                const FoldConst &k) {
         return (unsigned int)fold_fp64_from<PDOT>(f, p, t.y, k.nphi_d, k.n_phase) << SH;
     }
-    template <bool PDOT, bool K0, int SH>
+    template <bool PDOT, bool K0, int SH, bool RED>
     __device__ __forceinline__ static unsigned int offset(double p, const prep_t &t,
                                                           const FoldConst &k) {
-        return offset_from<PDOT, K0, SH>(fpart(p, t), p, t, k);
+        return offset_from<PDOT, K0, SH, RED>(fpart(p, t), p, t, k);
     }
     __device__ __forceinline__ static bool has_pdot(double2 t) { return t.y != 0.0; }
     __device__ __forceinline__ static bool k_zero(const prep_t &) { return true; }
@@ -126,16 +126,18 @@ template <> struct Fold<GCE_PHASE_SPLIT32> {
     __device__ __forceinline__ static fpart_t fpart(float4 p, const prep_t &t) {
         return fold_split_fpart(p, t);
     }
-    template <bool PDOT, bool K0, int SH>
+    // RED: re-reduce the residual without Pdot as well (narrow slot range)
+    template <bool PDOT, bool K0, int SH, bool RED>
     __device__ __forceinline__ static unsigned int offset_from(fpart_t f, float4 p,
                                                                const prep_t &t,
                                                                const FoldConst &k) {
-        return (unsigned int)(fold_split_from<PDOT>(f, p, t, k.nphi_f, k.zoff) + kSlotBias) << SH;
+        return (unsigned int)(fold_split_from<PDOT, RED>(f, p, t, k.nphi_f, k.zoff) + kSlotBias)
+               << SH;
     }
-    template <bool PDOT, bool K0, int SH>
+    template <bool PDOT, bool K0, int SH, bool RED>
     __device__ __forceinline__ static unsigned int offset(float4 p, const prep_t &t,
                                                           const FoldConst &k) {
-        return offset_from<PDOT, K0, SH>(fpart(p, t), p, t, k);
+        return offset_from<PDOT, K0, SH, RED>(fpart(p, t), p, t, k);
     }
     __device__ __forceinline__ static bool has_pdot(float4 t) {
         return t.z != 0.0f || t.w != 0.0f;
@@ -154,15 +156,15 @@ template <> struct Fold<GCE_PHASE_FIXED32> {
     __device__ __forceinline__ static fpart_t fpart(uint4 p, const prep_t &t) {
         return fold_fixed_fpart(p, t);
     }
-    template <bool PDOT, bool K0, int SH>
+    template <bool PDOT, bool K0, int SH, bool RED>
     __device__ __forceinline__ static unsigned int offset_from(fpart_t f, uint4 p, const prep_t &t,
                                                                const FoldConst &k) {
         return fold_fixed_bin_from<PDOT, K0>(f, p, t, (unsigned int)k.n_phase) << SH;
     }
-    template <bool PDOT, bool K0, int SH>
+    template <bool PDOT, bool K0, int SH, bool RED>
     __device__ __forceinline__ static unsigned int offset(uint4 p, const prep_t &t,
                                                           const FoldConst &k) {
-        return offset_from<PDOT, K0, SH>(fpart(p, t), p, t, k);
+        return offset_from<PDOT, K0, SH, RED>(fpart(p, t), p, t, k);
     }
     __device__ __forceinline__ static bool has_pdot(const FixedTrial &t) {
         return (t.i.z | t.i.w) != 0u;
@@ -186,7 +188,7 @@ __device__ __forceinline__ void compiler_fence() { asm volatile("" ::: "memory")
 // bins (their counts are sums of adjacent fine bins, formed in the epilogue).
 // SHARED: the thread's trials share their period (period-major tiles), so the
 // fold's period part is computed once per point for all of them.
-template <int MODE, int TPT, int SH, bool PDOT, bool K0, bool SHARED>
+template <int MODE, int TPT, int SH, bool PDOT, bool K0, bool RED, bool SHARED>
 __device__ __forceinline__ void count_points(
     const typename ModeTraits<MODE>::point_t *__restrict__ pts, int ka, int kb,
     const typename Fold<MODE>::prep_t (&tc)[TPT], const unsigned int (&base)[TPT],
@@ -199,21 +201,21 @@ __device__ __forceinline__ void count_points(
 #pragma unroll
         for (int s = 0; s < TPT; ++s) {
             const unsigned int addr =
-                base[s] + (SHARED ? Fold<MODE>::template offset_from<PDOT, K0, SH>(fp, p, tc[s], fk)
-                                  : Fold<MODE>::template offset<PDOT, K0, SH>(p, tc[s], fk));
+                base[s] + (SHARED ? Fold<MODE>::template offset_from<PDOT, K0, SH, RED>(fp, p, tc[s], fk)
+                                  : Fold<MODE>::template offset<PDOT, K0, SH, RED>(p, tc[s], fk));
             red_shared_inc(addr);
         }
     }
 }
 
-template <int MODE, int TPT, int SH, bool PDOT, bool K0>
+template <int MODE, int TPT, int SH, bool PDOT, bool K0, bool RED = false>
 __device__ __forceinline__ void count_points_any(
     bool shared, const typename ModeTraits<MODE>::point_t *__restrict__ pts, int ka, int kb,
     const typename Fold<MODE>::prep_t (&tc)[TPT], const unsigned int (&base)[TPT],
     const FoldConst &fk) {
     constexpr bool SH_OK = PDOT && TPT > 1;  // sharing pays only with a Pdot term
-    if (SH_OK && shared) count_points<MODE, TPT, SH, PDOT, K0, SH_OK>(pts, ka, kb, tc, base, fk);
-    else count_points<MODE, TPT, SH, PDOT, K0, false>(pts, ka, kb, tc, base, fk);
+    if (SH_OK && shared) count_points<MODE, TPT, SH, PDOT, K0, RED, SH_OK>(pts, ka, kb, tc, base, fk);
+    else count_points<MODE, TPT, SH, PDOT, K0, RED, false>(pts, ka, kb, tc, base, fk);
 }
 
 // c_ij of one phase bin at the end of a magnitude segment (low - snapshot), with
@@ -386,8 +388,9 @@ __global__ void __launch_bounds__(1 << LOG2B, main_min_blocks(TPT, LOG2B)) k_mai
     const int n_phase = a.n_phase, n_mag = a.n_mag;
     constexpr bool SPLIT = MODE == GCE_PHASE_SPLIT32;
     const int ovl = a.overlap ? 1 : 0;
-    const SlotRange zr = slot_range(MODE, n_phase);
-    const int n_slots = slots_per_trial(MODE, n_phase);
+    const bool narrow = SPLIT && a.narrow != 0;
+    const SlotRange zr = slot_range(MODE, n_phase, narrow);
+    const int n_slots = slots_per_trial(MODE, n_phase, narrow);
     const int slot_off = -zr.zmin;  // physical index of logical slot l: l + slot_off
     const int stride_j = B, stride_s = n_slots * B;
 
@@ -480,7 +483,7 @@ __global__ void __launch_bounds__(1 << LOG2B, main_min_blocks(TPT, LOG2B)) k_mai
                 if (tt[s] < a.n_trials) fm = fmaxf(fm, fabsf(split_fh(tc[s])));
             fm = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(fm)));
             int zlo, zhi;
-            split_slot_window(pdot, tau_max_f * fm, n_phase, zlo, zhi);
+            split_slot_window(pdot || narrow, tau_max_f * fm, n_phase, zlo, zhi);
             L = max(zlo, zr.zmin);
             R = min(zhi, zr.zmax);
         }
@@ -507,6 +510,7 @@ __global__ void __launch_bounds__(1 << LOG2B, main_min_blocks(TPT, LOG2B)) k_mai
                     const typename ModeTraits<MODE>::point_t *pp = s_pts;
                     if (k0) {
                         if (pdot) count_points_any<MODE, TPT, SH, true, true>(pdm, pp, ka - lo, kb - lo, tc, base, fk);
+                        else if (SPLIT && narrow) count_points_any<MODE, TPT, SH, false, true, SPLIT>(pdm, pp, ka - lo, kb - lo, tc, base, fk);
                         else count_points_any<MODE, TPT, SH, false, true>(pdm, pp, ka - lo, kb - lo, tc, base, fk);
                     } else if (MODE == GCE_PHASE_FIXED32) {
                         if (pdot) count_points_any<MODE, TPT, SH, true, false>(pdm, pp, ka - lo, kb - lo, tc, base, fk);
@@ -794,10 +798,10 @@ cudaError_t launch_for_block(int block, int grid, size_t smem, const MainArgs &a
 }  // namespace
 
 size_t main_smem_bytes(int mode, int block, int tpt, int chunk, int n_phase, int n_mag,
-                       int table_smem, int k, int overlap) {
+                       int table_smem, int k, int narrow) {
     size_t pt = mode == GCE_PHASE_FP64 ? 8 : 16;
     size_t b = pt * (size_t)chunk + 8 * (size_t)table_smem +
-               4 * (size_t)tpt * slots_per_trial(mode, n_phase) * block +
+               4 * (size_t)tpt * slots_per_trial(mode, n_phase, narrow != 0) * block +
                4 * (size_t)((n_mag + 2) & ~1) + 8 * (size_t)(block / 32) * (size_t)(k > 0 ? k : 1) +
                24 * (size_t)(block / 32);
     return b;

@@ -141,9 +141,9 @@ extern "C" gce_status gce_ce_topk_static(const double *times, const double *mags
     int chunk = (int)((n_max + 31) / 32 * 32);
     if (chunk > 1024) chunk = 1024;
     int table_smem = (int)(n_max + 1 < 1024 ? n_max + 1 : 1024);
+    const int narrow = (mode == GCE_PHASE_SPLIT32 && n_pdots > 1) ? 1 : 0;
     const size_t smem = main_smem_bytes(mode, block, tpt, chunk, cfg->n_phase_bins,
-                                        cfg->n_mag_bins, table_smem, k,
-                                        (cfg->flags & GCE_FLAG_OVERLAP) ? 1 : 0);
+                                        cfg->n_mag_bins, table_smem, k, narrow);
     int optin = 0;
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return fail(GCE_ERR_CUDA, cudaGetErrorString(e));
@@ -211,6 +211,7 @@ extern "C" gce_status gce_ce_topk_static(const double *times, const double *mags
     ma.n_tiles = (int)n_tiles;
     ma.n_ptiles = tg.n_ptiles;
     ma.pd_major = tg.pd_major;
+    ma.narrow = narrow;
     ma.n_items = n_items;
     ma.grab = 1;
     ma.n_phase = cfg->n_phase_bins;

@@ -149,6 +149,32 @@ def test_four_trials_per_thread_not_built_for_fp64(h):
     g.gce_set_tuning(h, g.Config(15, 10, "split32"), 500, block=128, tpt=4)
 
 
+@pytest.mark.parametrize("n_phase", [2, 15, 50])
+def test_split_narrow_slots_without_pdot(h, n_phase):
+    """A job with a Pdot axis keeps SPLIT32's narrow slot range, so its tiles whose Pdot
+    values are all 0 re-reduce the residual too: near the fold's cycle limit the grid
+    equals the one-Pdot grid (wide slot range) bit for bit and the oracle's."""
+    rng = np.random.default_rng(43)
+    n_obs, n_curves = 300, 3
+    ts = [np.sort(rng.uniform(0.0, 2.0e8, n_obs)) for _ in range(n_curves)]
+    ms = [15 + 0.3 * np.sin(2 * np.pi * t / 97.1) + rng.normal(0, 0.05, n_obs) for t in ts]
+    offs = np.arange(n_curves + 1, dtype=np.int64) * n_obs
+    periods = np.linspace(96.0, 500.0, 257)
+    mk = lambda pd: synth.LightCurveBatch("narrow", np.concatenate(ts), np.concatenate(ms), offs,
+                                          periods, np.asarray(pd), 15, 10, np.zeros(n_curves),
+                                          np.zeros(n_curves), np.zeros(n_curves))
+    cfg = g.Config(n_phase, 10, "split32")
+    for tpt in (1, 2, 4):  # flat tiles and period-major tiles
+        g.gce_set_tuning(h, cfg, n_obs, block=128, tpt=tpt, chunk=512)
+        two = g.gce_ce_grid(h, cfg=cfg, **dev_args(mk([0.0, 0.0]))).cpu().numpy()
+        one = g.gce_ce_grid(h, cfg=cfg, **dev_args(mk([0.0]))).cpu().numpy()
+        assert g.gce_stream_status(h) == g.GCE_OK
+        assert np.array_equal(two[:, 0], one[:, 0]) and np.array_equal(two[:, 1], one[:, 0])
+    ref, dmin = oracle.Oracle().ce_grid(np.concatenate(ts), np.concatenate(ms), offs, periods,
+                                        np.array([0.0]), n_phase, 10, with_dmin=True)
+    compare_grid("split32", one.astype(np.float64), ref, dmin)
+
+
 def test_host_checks_raise(h):
     b = small_batch()
     args = dev_args(b)
