@@ -95,3 +95,26 @@ def test_paper_scale_search(h):
                                          cc, ct)
     far = rd > 4 * EPS_PHASE["split32"]
     assert np.all(np.abs(rh - tH[curves].ravel())[far] <= TOL_H["split32"])
+
+
+@pytest.mark.parametrize("mode", ["split32", "fixed32"])
+def test_paper_scale_overlap_search(h, mode):
+    """The paper's production setting: Sec. 3's grid with 50 phase bins overlapping by
+    half (Sec. 2.3).  The device's top cells carry the oracle's H (overlapping bins)
+    and rho is finite for every curve."""
+    b = synth.make_config(5)
+    cfg = g.Config(50, 10, mode, overlap=True)
+    args = dev_args(b)
+    g.gce_autotune_job(h, cfg=cfg, **args)
+    tH, tI, mu, sd, rho = g.gce_ce_detect(h, cfg=cfg, k=3, **args)
+    assert g.gce_stream_status(h) == g.GCE_OK
+    tH, tI = tH.cpu().numpy().astype(np.float64), tI.cpu().numpy()
+    assert np.all(np.isfinite(rho.cpu().numpy()))
+    curves = np.arange(0, 100, 10)
+    cc = np.repeat(curves, 3)
+    ct = tI[curves].ravel()
+    rh, rd, _ = oracle.Oracle().ce_cells(b.times, b.mags, b.offsets, b.periods, b.pdots, 50, 10,
+                                         cc, ct, overlap=True)
+    far = rd > 4 * EPS_PHASE[mode]
+    assert far.mean() > 0.5
+    assert np.all(np.abs(rh - tH[curves].ravel())[far] <= TOL_H[mode])
