@@ -128,3 +128,16 @@ def test_band_count_range(h, mb, n_bands):
     with pytest.raises(g.GceError):
         g.gce_ce_grid_bands(h, bands=torch.tensor(bands, device="cuda"), n_bands=n_bands,
                             cfg=g.Config(15, 10, "fp64"), **dev_args(b))
+
+
+def test_multiband_signed_magnitudes(h):
+    """Values of both signs (the median's radix selection orders binary64 keys through
+    their sign bit): FP64 grid against the oracle."""
+    b, bands = synth.make_multiband(63, n_curves=6, n_obs=301, n_bands=2, n_periods=400)
+    b.mags = b.mags - 15.3  # straddles zero in every filter
+    z = oracle.Oracle().band_normalize(b.mags, bands, b.offsets, 2)
+    ref = oracle.Oracle().ce_grid(b.times, z, b.offsets, b.periods, b.pdots, 15, 10)
+    got = g.gce_ce_grid_bands(h, bands=torch.tensor(bands, device="cuda"), n_bands=2,
+                              cfg=g.Config(15, 10, "fp64"), **dev_args(b))
+    assert g.gce_stream_status(h) == g.GCE_OK
+    assert np.abs(got.cpu().numpy().astype(np.float64) - ref).max() <= TOL_H["fp64"]
