@@ -175,6 +175,27 @@ def test_split_narrow_slots_without_pdot(h, n_phase):
     compare_grid("split32", one.astype(np.float64), ref, dmin)
 
 
+@pytest.mark.parametrize("mode", MODES)
+def test_longest_curve(h, mode):
+    """A curve of the maximum length (65,535 points: counts above the 2048 c ln c entries
+    kept in shared memory read the table from global memory, and the points are staged
+    in many chunks) beside a 3-point curve, with and without a Pdot axis."""
+    rng = np.random.default_rng(44)
+    n_long = 65535
+    t_long = np.sort(rng.uniform(0.0, 9e7, n_long))
+    m_long = 15 + 0.3 * np.sin(2 * np.pi * t_long / 1234.5) + rng.normal(0, 0.05, n_long)
+    t_short, m_short = np.array([1e6, 2e6, 3.5e6]), np.array([15.0, 15.4, 15.1])
+    offs = np.array([0, n_long, n_long + 3], dtype=np.int64)
+    for pdots in ((0.0,), (0.0, -2e-11)):
+        b = synth.LightCurveBatch("long", np.r_[t_long, t_short], np.r_[m_long, m_short], offs,
+                                  synth.log_periods(600.0, 3000.0, 64), np.asarray(pdots), 15, 10,
+                                  np.zeros(2), np.zeros(2), np.zeros(2))
+        got = gpu_grid(h, dev_args(b), mode)
+        ref, dmin = oracle.Oracle().ce_grid(b.times, b.mags, b.offsets, b.periods, b.pdots, 15,
+                                            10, with_dmin=True)
+        compare_grid(mode, got, ref, dmin)
+
+
 def test_host_checks_raise(h):
     b = small_batch()
     args = dev_args(b)
