@@ -54,6 +54,17 @@ __device__ __forceinline__ unsigned long long tab_lookup(const unsigned long lon
     if (ALL_SMEM) return s_tab[c];
     return c < table_smem ? s_tab[c] : __ldg(g_tab + c);
 }
+// The same from d = c << 16 (low 16 bits zero): the byte offset c * 8 is d >> 13.
+template <bool ALL_SMEM>
+__device__ __forceinline__ unsigned long long tab_lookup16(const unsigned long long *s_tab,
+                                                           int table_smem,
+                                                           const unsigned long long *g_tab,
+                                                           unsigned int d) {
+    if (ALL_SMEM)
+        return *reinterpret_cast<const unsigned long long *>(
+            reinterpret_cast<const char *>(s_tab) + (d >> 13));
+    return tab_lookup<false>(s_tab, table_smem, g_tab, (int)(d >> 16));
+}
 
 
 // Per-mode constants of the fold, computed once per kernel.
@@ -280,11 +291,11 @@ struct BinWindow {
                         first[s] = d;
                         t[s][g] = 0ull;
                     } else {
-                        t[s][g] = tab_lookup<ALL_SMEM>(s_tab, table_smem, g_tab, (int)((prev[s] + d) >> 16));
+                        t[s][g] = tab_lookup16<ALL_SMEM>(s_tab, table_smem, g_tab, prev[s] + d);
                     }
                     prev[s] = d;
                 } else {
-                    t[s][g] = tab_lookup<ALL_SMEM>(s_tab, table_smem, g_tab, (int)(d >> 16));
+                    t[s][g] = tab_lookup16<ALL_SMEM>(s_tab, table_smem, g_tab, d);
                 }
             }
         if (OVL) started = true;
@@ -297,9 +308,12 @@ struct BinWindow {
                     for (int k = 0; k < C; ++k) *p[s][g][k] = __byte_perm(v[s][g][k], 0u, 0x1010);
         }
 #pragma unroll
-        for (int s = 0; s < TPT; ++s)
+        for (int s = 0; s < TPT; ++s) {
+            unsigned long long sum = t[s][0];
 #pragma unroll
-            for (int g = 0; g < G; ++g) acc[s] += t[s][g];
+            for (int g = 1; g < G; ++g) sum += t[s][g];
+            acc[s] += sum;
+        }
     }
 
     __device__ __forceinline__ void sum(int n, int L, int R, unsigned long long (&acc)[TPT]) {
