@@ -46,6 +46,19 @@ def test_multiband_grid(h, mb, mode):
 
 
 @pytest.mark.parametrize("mode", MODES)
+def test_multiband_overlapping_bins(h, mb, mode):
+    """Multi-filter input with the paper's 50 half-overlapping phase bins."""
+    b, bands, _, _ = mb
+    z = oracle.Oracle().band_normalize(b.mags, bands, b.offsets, 3)
+    ref, dmin = oracle.Oracle().ce_grid(b.times, z, b.offsets, b.periods, b.pdots, 50, 10,
+                                        with_dmin=True, overlap=True)
+    got = g.gce_ce_grid_bands(h, bands=torch.tensor(bands, device="cuda"), n_bands=3,
+                              cfg=g.Config(50, 10, mode, overlap=True), **dev_args(b))
+    assert g.gce_stream_status(h) == g.GCE_OK
+    compare_grid(mode, got.cpu().numpy().astype(np.float64), ref, dmin)
+
+
+@pytest.mark.parametrize("mode", MODES)
 def test_multiband_detect(h, mb, mode):
     b, bands, ref, dmin = mb
     k = 4

@@ -74,11 +74,12 @@ def test_overlap_needs_two_bins(h):
         g.gce_ce_grid(h, cfg=g.Config(1, 10, "fp64", overlap=True), **dev_args(b))
 
 
+@pytest.mark.parametrize("overlap", [False, True])
 @pytest.mark.parametrize("mode", MODES)
-def test_significance(h, mode):
+def test_significance(h, mode, overlap):
     b = batch(seed=22, n_curves=5, n_periods=3001)  # several tiles with a ragged tail
     args = dev_args(b)
-    cfg = g.Config(15, 10, mode)
+    cfg = g.Config(15, 10, mode, overlap=overlap)
     k = 4
     tH, tI, mu, sd, rho = g.gce_ce_detect(h, cfg=cfg, k=k, **args)
     assert g.gce_stream_status(h) == g.GCE_OK
@@ -92,7 +93,8 @@ def test_significance(h, mode):
     assert np.all(np.abs(sd - gs) <= 1e-4 * gs)
     assert np.all(np.abs(rho - gr) <= 1e-3 * np.maximum(1.0, gr))
     # against the oracle
-    ref = oracle.Oracle().ce_grid(b.times, b.mags, b.offsets, b.periods, b.pdots, 15, 10)
+    ref = oracle.Oracle().ce_grid(b.times, b.mags, b.offsets, b.periods, b.pdots, 15, 10,
+                                  overlap=overlap)
     om, osd, orho = oracle.oracle_significance(ref)
     if mode == "fp64":
         assert np.all(np.abs(mu - om) <= 2e-6)
