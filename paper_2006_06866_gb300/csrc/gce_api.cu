@@ -343,7 +343,9 @@ gce_status make_plan(gce_handle h, const Job &j, Plan &pl) {
     long long g = (long long)h->n_sm * occ;
     g = std::min(g, std::max(pl.n_items, 1ll));
     pl.grid = (int)g;
-    long long grab = pl.n_items / (g * 32);
+    // about 128 grabs per CTA: large enough to amortise the counter, small enough
+    // that the last grabs leave little tail
+    long long grab = pl.n_items / (g * 128);
     pl.grab = (int)std::max(1ll, std::min(grab, 64ll));
     return GCE_OK;
 }
