@@ -73,20 +73,14 @@ struct FoldConst {
     float nphi_f;
     float zoff;          // SPLIT32: 1.5 2^23 + n_phase
     int n_phase;
-    int sh;              // log2 of the byte stride between a thread's slots
-    unsigned int n_sh;   // FIXED32: n_phase << sh
-    unsigned int mask;   // FIXED32: ~(2^sh - 1)
 };
 
-__device__ __forceinline__ FoldConst fold_const(int n_phase, int sh) {
+__device__ __forceinline__ FoldConst fold_const(int n_phase) {
     FoldConst k;
     k.nphi_d = (double)n_phase;
     k.nphi_f = (float)n_phase;
     k.zoff = kRound + (float)n_phase;
     k.n_phase = n_phase;
-    k.sh = sh;
-    k.n_sh = (unsigned int)n_phase << sh;
-    k.mask = ~((1u << sh) - 1u);
     return k;
 }
 
@@ -421,7 +415,7 @@ __global__ void __launch_bounds__(1 << LOG2B, main_min_blocks(TPT, LOG2B)) k_mai
     const point_t *g_pts = reinterpret_cast<const point_t *>(a.payload);
     const trial_t *g_tr = reinterpret_cast<const trial_t *>(a.trialc);
     unsigned int *my_cnt = s_cnt + tid;
-    const FoldConst fk = fold_const(n_phase, SH);
+    const FoldConst fk = fold_const(n_phase);
     unsigned int base[TPT];
     unsigned int *wbase[TPT];  // physical slot 0 of trial s
 #pragma unroll
@@ -767,7 +761,7 @@ __global__ void k_counts(MainArgs a, long long n_cells, const long long *cell_cu
     const int *seg = a.seg + c * (a.n_mag + 1);
     unsigned int *out = counts + cell * a.n_mag * a.n_phase;
     const bool pdot = Fold<MODE>::has_pdot(tr0);
-    const FoldConst fk = fold_const(a.n_phase, 0);
+    const FoldConst fk = fold_const(a.n_phase);
     for (int i = 0; i < a.n_mag; ++i) {
         for (int k = seg[i]; k < seg[i + 1]; ++k) {
             int j = (pdot ? Fold<MODE>::template raw_slot<true>(pts[k], tr, fk)
