@@ -18,6 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libgce.so")
+CHECKED_MARK = os.path.join(OUT_DIR, "CHECKED")  # present while LIB is a checked build
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               *ARCH]
@@ -40,19 +41,24 @@ def _deps():
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or os.path.exists(CHECKED_MARK):
         return False
     t = os.path.getmtime(LIB)
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    if not force and up_to_date():
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False,
+          checked: bool = False) -> str:
+    """checked: compile the counter-slot bounds check into the hot loop (every
+    increment's slot tested against the trial's kept range; a miss is reported
+    by gce_stream_status and the access skipped).  For verification runs only:
+    it costs a few instructions per point-trial."""
+    if not force and not checked and up_to_date():
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
     tool = nvcc()
     objs = []
-    extra = ["-Xptxas", "-v"] if ptxas_info else []
+    extra = (["-Xptxas", "-v"] if ptxas_info else []) + (["-DGCE_CHECK_SLOTS"] if checked else [])
 
     def compile_one(src):
         obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
@@ -75,8 +81,13 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     os.replace(tmp, LIB)
     for o in objs:
         os.remove(o)
+    if checked:
+        open(CHECKED_MARK, "w").close()
+    elif os.path.exists(CHECKED_MARK):
+        os.remove(CHECKED_MARK)
     return LIB
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv,
+                checked="--checked" in sys.argv))

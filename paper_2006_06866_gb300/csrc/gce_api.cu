@@ -592,6 +592,8 @@ gce_status state_status(gce_handle h) {
                     (e & ERR_BAND) ? "filter index >= n_bands; " : "");
     if (e & ERR_RANGE)
         return fail(h, GCE_ERR_UNSUPPORTED, "device check: trial range beyond the phase fold's range");
+    if (e & ERR_SLOT)
+        return fail(h, GCE_ERR_CUDA, "checked build: a counter slot outside the kept range");
     return GCE_OK;
 }
 

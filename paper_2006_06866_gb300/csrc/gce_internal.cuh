@@ -31,6 +31,7 @@ enum : unsigned int {
     ERR_PDOT = 4u,      // non-finite period derivative
     ERR_RANGE = 8u,     // trial range beyond what the chosen fold represents
     ERR_BAND = 16u,     // filter index outside [0, n_bands)
+    ERR_SLOT = 32u,     // checked builds only: a counter slot outside the trial's kept range
 };
 
 // Fixed-point scaling of the FIXED32 fold, derived from the job's maxima.

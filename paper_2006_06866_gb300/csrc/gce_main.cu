@@ -73,6 +73,11 @@ struct FoldConst {
     float nphi_f;
     float zoff;          // SPLIT32: 1.5 2^23 + n_phase
     int n_phase;
+#if defined(GCE_CHECK_SLOTS)
+    // checked builds: the trial's kept logical slots and where to flag a miss
+    int zmin, zmax;
+    unsigned int *err;
+#endif
 };
 
 __device__ __forceinline__ FoldConst fold_const(int n_phase) {
@@ -208,6 +213,16 @@ __device__ __forceinline__ void count_points(
             const unsigned int addr =
                 base[s] + (SHARED ? Fold<MODE>::template offset_from<PDOT, K0, SH, RED>(fp, p, tc[s], fk)
                                   : Fold<MODE>::template offset<PDOT, K0, SH, RED>(p, tc[s], fk));
+#if defined(GCE_CHECK_SLOTS)
+            // checked builds: the logical slot of this increment must lie in the
+            // kept range; a miss is flagged and the access skipped
+            const int lslot =
+                (int)(addr - (base[s] + ((unsigned int)Fold<MODE>::kSlotBias << SH))) >> SH;
+            if (lslot < fk.zmin || lslot > fk.zmax) {
+                atomicOr(fk.err, (unsigned int)ERR_SLOT);
+                continue;
+            }
+#endif
             red_shared_inc(addr);
         }
     }
@@ -415,7 +430,14 @@ __global__ void __launch_bounds__(1 << LOG2B, main_min_blocks(TPT, LOG2B)) k_mai
     const point_t *g_pts = reinterpret_cast<const point_t *>(a.payload);
     const trial_t *g_tr = reinterpret_cast<const trial_t *>(a.trialc);
     unsigned int *my_cnt = s_cnt + tid;
+#if defined(GCE_CHECK_SLOTS)
+    FoldConst fk = fold_const(n_phase);
+    fk.zmin = zr.zmin;
+    fk.zmax = zr.zmax;
+    fk.err = &a.state->err;
+#else
     const FoldConst fk = fold_const(n_phase);
+#endif
     unsigned int base[TPT];
     unsigned int *wbase[TPT];  // physical slot 0 of trial s
 #pragma unroll

@@ -237,5 +237,6 @@ extern "C" gce_status gce_ce_topk_static(const double *times, const double *mags
     if (err & (ERR_TIME | ERR_PERIOD | ERR_PDOT))
         return fail(GCE_ERR_INVALID, "device check: non-finite or non-positive input values");
     if (err & ERR_RANGE) return fail(GCE_ERR_UNSUPPORTED, "device check: trial range beyond the fold");
+    if (err & ERR_SLOT) return fail(GCE_ERR_CUDA, "checked build: a counter slot outside the kept range");
     return GCE_OK;
 }
