@@ -199,12 +199,16 @@ def oracle_significance(grid):
     """Eq. 5 per curve from an oracle grid H[c, q, p]: rho = (mu - H_min) / sigma with
     mu and sigma the mean and population standard deviation (ddof 0; the paper
     does not say which) of all of the curve's CE values.  Returns (mu, sigma,
-    rho); rho is 0 where sigma is 0."""
+    rho); rho is 0 where sigma is 0.  The moments are taken of H - H_min (the
+    standard deviation does not depend on the shift, and mu - H_min is the mean of
+    the shifted values), so a flat grid has sigma = 0 exactly."""
     flat = grid.reshape(grid.shape[0], -1)
-    mu = flat.mean(axis=1)
-    sd = flat.std(axis=1)
-    rho = np.where(sd > 0, (mu - flat.min(axis=1)) / np.where(sd > 0, sd, 1.0), 0.0)
-    return mu, sd, rho
+    h_min = flat.min(axis=1)
+    d = flat - h_min[:, None]
+    gap = d.mean(axis=1)
+    sd = d.std(axis=1)
+    rho = np.where(sd > 0, gap / np.where(sd > 0, sd, 1.0), 0.0)
+    return h_min + gap, sd, rho
 
 
 def oracle_topk(grid, k):

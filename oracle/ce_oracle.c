@@ -206,7 +206,9 @@ static void cell_counts_from_bins(const double *t, const int32_t *mag_bins, int6
         double y;
         int32_t j = oracle_phase_bin(tau, f, a, n_phase, &y);
         counts[(int64_t)mag_bins[k] * n_phase + j] += 1;
-        if (overlap) counts[(int64_t)mag_bins[k] * n_phase + (j + n_phase - 1) % n_phase] += 1;
+        /* 13: the second (overlapping) bin dropped; 14: no wrap from bin 0 to bin n_phase - 1 */
+        if (overlap && !MUTANT(13) && !(MUTANT(14) && j == 0))
+            counts[(int64_t)mag_bins[k] * n_phase + (j + n_phase - 1) % n_phase] += 1;
         double fr = y - floor(y);
         double d = fr < 1.0 - fr ? fr : 1.0 - fr;
         d /= (double)n_phase;

@@ -523,11 +523,45 @@ def pin_band_normalization(orc):
     return out
 
 
+def pin_selection(orc):
+    """Selection and Eq. 5 on grids with known answers.  Top-k: brute force over
+    (H, flat index) pairs with Python's tuple order on grids full of ties, so
+    equal H go to the smaller flat index q * n_periods + p.  Significance: a grid
+    holding 0, 1, ..., n - 1 in any order has mean (n - 1)/2, population variance
+    (n^2 - 1)/12 and minimum 0; a flat grid has rho = 0."""
+    import oracle as oracle_mod
+    rng = np.random.default_rng(53)
+    ok = True
+    for _ in range(30):
+        n_c, n_q, n_p = (int(v) for v in rng.integers(1, 6, 3))
+        k = int(rng.integers(1, n_q * n_p + 1))
+        grid = rng.integers(0, 3, (n_c, n_q, n_p)).astype(np.float64)
+        h, idx = oracle_mod.oracle_topk(grid, k)
+        for c in range(n_c):
+            pairs = sorted((grid[c, q, p], q * n_p + p) for q in range(n_q) for p in range(n_p))
+            ok &= [i for _, i in pairs[:k]] == list(idx[c])
+            ok &= [v for v, _ in pairs[:k]] == list(h[c])
+    out = [("top-k: k smallest by (H, flat index), ties to the smaller index", bool(ok), "")]
+    worst = 0.0
+    for n in (2, 3, 10, 97, 1000):
+        grid = rng.permutation(n).astype(np.float64).reshape(1, 1, n)
+        mu, sd, rho = oracle_mod.oracle_significance(grid)
+        want_sd = ((n * n - 1) / 12.0) ** 0.5
+        worst = max(worst, abs(mu[0] - (n - 1) / 2.0), abs(sd[0] - want_sd) / want_sd,
+                    abs(rho[0] - (n - 1) / 2.0 / want_sd))
+    _, _, flat_rho = oracle_mod.oracle_significance(np.full((1, 2, 3), 0.7))
+    out.append(("Eq. 5 on 0..n-1: mean (n-1)/2, population variance (n^2-1)/12",
+                worst < 1e-12, f"worst {worst:.3g}"))
+    out.append(("Eq. 5 on a flat grid: rho = 0", flat_rho[0] == 0.0, ""))
+    return out
+
+
 ALL_PINS = (
     pin_fold_exact_rational, pin_fold_edges, pin_pdot_zero_plain_fold, pin_eq6_dephasing,
     pin_mag_bins, pin_entropy_chain_rule, pin_entropy_special_cases,
     pin_entropy_bounds_and_invariance, pin_brute_force_tiny, pin_paper_worked_example,
     pin_recovery, pin_overlapping_bins, pin_significance, pin_band_normalization,
+    pin_selection,
 )
 
 
