@@ -118,3 +118,29 @@ def test_significance_separates_signal_from_noise(h):
                                b.truth_p0, b.truth_pdot, b.truth_class)
     _, _, _, _, rho_n = g.gce_ce_detect(h, cfg=g.Config(15, 10, "split32"), k=1, **dev_args(nb))
     assert float(rho_s.min()) > 10.0 and float(rho_n.max()) < 10.0
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_significance_flat_grid(h, mode):
+    """A curve whose grid is flat (constant magnitudes, or a single point: H = 0 in
+    every cell) has sigma = 0 and rho = 0 exactly on the device, as in the oracle;
+    the other curves of the batch are unaffected."""
+    b = batch(seed=23, n_curves=3, n_periods=1500)
+    n0 = int(b.offsets[1])
+    mags = b.mags.copy()
+    mags[:n0] = 15.25
+    times = np.r_[b.times, 1234.5]
+    mags = np.r_[mags, 16.0]
+    offs = np.r_[b.offsets, b.offsets[-1] + 1].astype(np.int64)
+    fb = synth.LightCurveBatch("flat", times, mags, offs, b.periods, b.pdots, 15, 10,
+                               np.zeros(4), np.zeros(4), np.zeros(4))
+    tH, _, mu, sd, rho = g.gce_ce_detect(h, cfg=g.Config(15, 10, mode), k=3, **dev_args(fb))
+    assert g.gce_stream_status(h) == g.GCE_OK
+    mu, sd, rho = mu.cpu().numpy(), sd.cpu().numpy(), rho.cpu().numpy()
+    for c in (0, 3):
+        assert tH[c].abs().max().item() == 0.0
+        assert mu[c] == 0.0 and sd[c] == 0.0 and rho[c] == 0.0
+    ref = oracle.Oracle().ce_grid(fb.times, fb.mags, fb.offsets, fb.periods, fb.pdots, 15, 10)
+    om, osd, orho = oracle.oracle_significance(ref)
+    assert osd[0] == 0.0 and orho[0] == 0.0 and osd[3] == 0.0 and orho[3] == 0.0
+    assert np.all(np.abs(rho[1:3] - orho[1:3]) <= 5e-2 * np.maximum(1.0, orho[1:3]))
