@@ -22,6 +22,7 @@ GCE_FLAG_NO_GRAPH = 1
 GCE_FLAG_TIME_KERNEL = 2
 GCE_FLAG_OVERLAP = 4
 GCE_MAX_PHASE_BINS, GCE_MAX_MAG_BINS, GCE_MAX_CURVE_POINTS, GCE_MAX_TOPK = 256, 255, 65535, 64
+GCE_MAX_BANDS = 8
 MODES = {"fp64": GCE_PHASE_FP64, "split32": GCE_PHASE_SPLIT32, "fixed32": GCE_PHASE_FIXED32}
 
 

@@ -33,6 +33,17 @@ def test_header_declares_the_bound_symbols():
     assert decl == sorted(binding.SIGNATURES), (decl, sorted(binding.SIGNATURES))
 
 
+def test_header_constants_match_the_binding():
+    """Every #define GCE_* and enum value of the header has the binding's value."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    consts = {k: int(v) for k, v in re.findall(r"#define\s+(GCE_[A-Z_0-9]+)\s+(\d+)u?\b", text)}
+    consts.update({k: int(v) for k, v in re.findall(r"\b(GCE_[A-Z_0-9]+)\s*=\s*(\d+)", text)})
+    assert len(consts) >= 14, consts
+    for name, value in consts.items():
+        assert getattr(binding, name) == value, name
+        assert getattr(g, name) == value, name
+
+
 def test_every_declared_symbol_is_exported(L):
     for name in declared_functions():
         assert hasattr(L, name), name

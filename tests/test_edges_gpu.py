@@ -260,3 +260,29 @@ def test_autotune_keeps_results(h):
     assert g.gce_get_tuning(h, cfg, 500) == g.gce_get_tuning(h, cfg, 500, n_pdots=8)
     with pytest.raises(g.GceError):
         g.gce_get_tuning(h, cfg, 500, n_pdots=0)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_topk_limits(h, mode):
+    """k at its maximum (GCE_MAX_TOPK over several trial tiles) and k = every trial of
+    a small grid: the device top-k is exactly the k smallest cells of the device grid,
+    ties to the smaller flat index; larger k is refused before any launch."""
+    for n_periods, pdots, k in ((700, (0.0, -1e-11), g.GCE_MAX_TOPK), (20, (0.0,), 20)):
+        b = small_batch(seed=9, n_periods=n_periods, pdots=pdots)
+        args = dev_args(b)
+        cfg = g.Config(15, 10, mode)
+        grid = gpu_grid(h, args, mode).reshape(b.n_curves, -1)
+        for detect in (False, True):
+            if detect:
+                tH, tI, _, _, _ = g.gce_ce_detect(h, cfg=cfg, k=k, **args)
+            else:
+                tH, tI = g.gce_ce_topk(h, cfg=cfg, k=k, **args)
+            assert g.gce_stream_status(h) == g.GCE_OK
+            tH, tI = tH.cpu().numpy().astype(np.float64), tI.cpu().numpy()
+            for c in range(b.n_curves):
+                order = np.lexsort((np.arange(grid.shape[1]), grid[c]))[:k]
+                assert np.array_equal(tI[c], order), (c, detect)
+                assert np.array_equal(tH[c], grid[c, order])
+        for bad in (min(k + 1, grid.shape[1] + 1), g.GCE_MAX_TOPK + 1):
+            with pytest.raises(g.GceError):
+                g.gce_ce_topk(h, cfg=cfg, k=bad, **args)
