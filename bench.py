@@ -75,6 +75,9 @@ def parse():
     ap.add_argument("--bands", type=int, default=0,
                     help="multi-filter input: give every point one of N filters (seeded) and "
                          "search through gce_ce_detect_bands (0 = single filter)")
+    ap.add_argument("--pdots", type=int, default=0,
+                    help="override the Pdot-axis length of workloads 2, 4 and 5 (Sec. 3 runs "
+                         "32, 128 and 512; 0 = the workload's)")
     ap.add_argument("--shape", default="",
                     help="block,tpt,chunk: fixed launch shape instead of autotuning (profiling runs)")
     return ap.parse_args()
@@ -101,6 +104,15 @@ def profiled_traffic(mode, workload, n_curves):
     if rec.get("kernel_sources_sha256_16") != h.hexdigest()[:16]:
         return None
     return int(rec["traffic_bytes_full_launch"]) if "traffic_bytes_full_launch" in rec else None
+
+
+def workload_overrides(args):
+    """Keyword overrides of synth.make_config from the command line."""
+    if not args.pdots:
+        return {}
+    if args.workload not in (2, 4, 5):
+        raise SystemExit("--pdots applies to workloads 2, 4 and 5 (the ones with a Pdot axis)")
+    return {"n_pdots": int(args.pdots)}
 
 
 def dist_env():
@@ -159,7 +171,7 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     import synth
-    batch = synth.make_config(args.workload)
+    batch = synth.make_config(args.workload, **workload_overrides(args))
     per_step = max(0.5, args.ref_seconds / max(1, args.steps + args.warmup))
     rates = []
     used = 1
@@ -261,7 +273,7 @@ def main():
         if pg is not None:
             pg.barrier()
 
-    batch = synth.make_config(args.workload)
+    batch = synth.make_config(args.workload, **workload_overrides(args))
     if args.curves:
         batch = batch.subset(list(range(min(args.curves, batch.n_curves))))
     if world > 1:

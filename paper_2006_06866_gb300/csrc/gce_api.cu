@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "gce_internal.cuh"
+#include "gce_topk.cuh"
 
 using namespace gce;
 
@@ -51,7 +52,7 @@ struct gce_handle_s {
     int smem_optin = 0;
     std::string last_error;
     DevBuf payload, seg, trialc, order, offsets, cand, stats, table, state, in_times, in_mags,
-        in_periods, in_pdots, out_H, out_idx, band_stats;
+        in_periods, in_pdots, out_H, out_idx, band_stats, cand2, stats2;
     int table_n = -1;                    // largest count the table covers
     int *h_order = nullptr;              // pinned staging
     long long *h_offsets = nullptr;
@@ -111,6 +112,14 @@ static gce_status ensure(gce_handle h, DevBuf &b, size_t bytes) {
 }
 
 static int point_bytes(int mode) { return mode == GCE_PHASE_FP64 ? 8 : 16; }
+
+static size_t trial_bytes(int mode) {
+    switch (mode) {
+        case GCE_PHASE_FP64: return sizeof(ModeTraits<GCE_PHASE_FP64>::trial_t);
+        case GCE_PHASE_SPLIT32: return sizeof(ModeTraits<GCE_PHASE_SPLIT32>::trial_t);
+        default: return sizeof(ModeTraits<GCE_PHASE_FIXED32>::trial_t);
+    }
+}
 
 static int ilog2_ceil(long long v) {
     int e = 0;
@@ -228,7 +237,8 @@ extern "C" gce_status gce_destroy(gce_handle h) {
     for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
     DevBuf *bufs[] = {&h->payload, &h->seg, &h->trialc, &h->order, &h->offsets, &h->cand, &h->stats,
                       &h->table, &h->state, &h->in_times, &h->in_mags, &h->in_periods,
-                      &h->in_pdots, &h->out_H, &h->out_idx, &h->band_stats};
+                      &h->in_pdots, &h->out_H, &h->out_idx, &h->band_stats, &h->cand2,
+                      &h->stats2};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (h->h_order) cudaFreeHost(h->h_order);
@@ -266,6 +276,7 @@ struct Job {
 struct Plan {
     long long n_points, n_trials, n_items;
     int n_max, n_tiles, n_ptiles, pd_major, narrow, block, tpt, grid, chunk, table_smem, grab;
+    int n_groups, tiles_per_group;  // top-k: first merge level (0 groups: none)
     size_t smem;
 };
 
@@ -310,6 +321,8 @@ gce_status make_plan(gce_handle h, const Job &j, Plan &pl) {
     pl.n_ptiles = tg.n_ptiles;
     pl.pd_major = tg.pd_major;
     pl.n_items = (long long)j.n_curves * pl.n_tiles;
+    pl.n_groups = j.kind == JOB_TOPK ? topk_groups(pl.n_tiles, j.k, &pl.tiles_per_group) : 0;
+    if (j.kind != JOB_TOPK) pl.tiles_per_group = 0;
     CUDA_TRY(h, main_kernel_attrs(cfg->phase_mode, pl.tpt, pl.block, pl.smem));
     const void *kern = main_kernel_ptr(cfg->phase_mode, pl.tpt, pl.block);
     int occ = 0;
@@ -436,9 +449,21 @@ gce_status enqueue(gce_handle h, const Job &j, const Plan &pl, cudaStream_t s, b
             if (timed && (ms = mark(h, h->k0, s, capturing)) != GCE_OK) return ms;
             CUDA_TRY(h, launch_main(mode, pl.tpt, pl.block, pl.grid, pl.smem, ma, s));
             if (timed && (ms = mark(h, h->k1, s, capturing)) != GCE_OK) return ms;
-            CUDA_TRY(h, launch_topk_merge((const unsigned long long *)h->cand.p, j.n_curves,
-                                          pl.n_tiles, j.k, j.topk_H, (long long *)j.topk_idx,
-                                          ma.stats, j.mean, j.std_dev, j.rho, st, s));
+            if (pl.n_groups > 0) {
+                // many tiles per curve: reduce groups of tiles first, then merge the groups
+                TileStats *stats2 = j.rho ? (TileStats *)h->stats2.p : nullptr;
+                CUDA_TRY(h, launch_topk_reduce((const unsigned long long *)h->cand.p, j.n_curves,
+                                               pl.n_tiles, j.k, pl.tiles_per_group, pl.n_groups,
+                                               ma.stats, (unsigned long long *)h->cand2.p, stats2,
+                                               st, s));
+                CUDA_TRY(h, launch_topk_merge((const unsigned long long *)h->cand2.p, j.n_curves,
+                                              pl.n_groups, j.k, j.topk_H, (long long *)j.topk_idx,
+                                              stats2, j.mean, j.std_dev, j.rho, st, s));
+            } else {
+                CUDA_TRY(h, launch_topk_merge((const unsigned long long *)h->cand.p, j.n_curves,
+                                              pl.n_tiles, j.k, j.topk_H, (long long *)j.topk_idx,
+                                              ma.stats, j.mean, j.std_dev, j.rho, st, s));
+            }
             break;
         case JOB_SINGLE:
             ma.out = j.out;
@@ -488,7 +513,7 @@ gce_status run_job(gce_handle h, const Job &j, cudaStream_t s) {
     // workspace
     if ((st = ensure(h, h->payload, (size_t)point_bytes(mode) * pl.n_points)) != GCE_OK) return st;
     if ((st = ensure(h, h->seg, sizeof(int) * (size_t)j.n_curves * (j.cfg->n_mag_bins + 1))) != GCE_OK) return st;
-    if ((st = ensure(h, h->trialc, 32 * (size_t)pl.n_trials)) != GCE_OK) return st;
+    if ((st = ensure(h, h->trialc, trial_bytes(mode) * (size_t)pl.n_trials)) != GCE_OK) return st;
     if ((st = ensure(h, h->order, sizeof(int) * (size_t)j.n_curves)) != GCE_OK) return st;
     if ((st = ensure(h, h->offsets, sizeof(long long) * (size_t)(j.n_curves + 1))) != GCE_OK) return st;
     if (j.bands &&
@@ -499,6 +524,12 @@ gce_status run_job(gce_handle h, const Job &j, cudaStream_t s) {
         return st;
     if (j.kind == JOB_TOPK && j.rho &&
         (st = ensure(h, h->stats, sizeof(TileStats) * (size_t)j.n_curves * pl.n_tiles)) != GCE_OK)
+        return st;
+    if (j.kind == JOB_TOPK && pl.n_groups > 0 &&
+        (st = ensure(h, h->cand2, 8 * (size_t)j.n_curves * pl.n_groups * j.k)) != GCE_OK)
+        return st;
+    if (j.kind == JOB_TOPK && pl.n_groups > 0 && j.rho &&
+        (st = ensure(h, h->stats2, sizeof(TileStats) * (size_t)j.n_curves * pl.n_groups)) != GCE_OK)
         return st;
     if (pl.n_max > h->table_n) {
         if ((st = ensure(h, h->table, 8 * (size_t)(pl.n_max + 1))) != GCE_OK) return st;

@@ -286,3 +286,29 @@ def test_topk_limits(h, mode):
         for bad in (min(k + 1, grid.shape[1] + 1), g.GCE_MAX_TOPK + 1):
             with pytest.raises(g.GceError):
                 g.gce_ce_topk(h, cfg=cfg, k=bad, **args)
+
+
+@pytest.mark.parametrize("mode", ["split32", "fixed32"])
+def test_topk_two_level_merge(h, mode):
+    """Grids with thousands of trial tiles per curve are merged in two levels (groups
+    of tiles first, then the groups): the top-k is still exactly the k smallest cells
+    of the device grid, and the merged moments match the grid's own statistics."""
+    for n_periods, pdots, k in ((1_000_000, (0.0, -1e-11), 5), (200_000, (0.0, 2e-12), 64)):
+        b = small_batch(seed=11, n_curves=3, n_obs=90, n_periods=n_periods, pdots=pdots)
+        args = dev_args(b)
+        cfg = g.Config(15, 10, mode)
+        grid = gpu_grid(h, args, mode).reshape(b.n_curves, -1)
+        tH, tI, mu, sd, rho = g.gce_ce_detect(h, cfg=cfg, k=k, **args)
+        assert g.gce_stream_status(h) == g.GCE_OK
+        rH, rI = g.gce_ce_topk(h, cfg=cfg, k=k, **args)
+        assert torch.equal(tH, rH) and torch.equal(tI, rI)
+        tH, tI = tH.cpu().numpy().astype(np.float64), tI.cpu().numpy()
+        for c in range(b.n_curves):
+            order = np.lexsort((np.arange(grid.shape[1]), grid[c]))[:k]
+            assert np.array_equal(tI[c], order), c
+            assert np.array_equal(tH[c], grid[c, order])
+        gm, gs, gr = oracle.oracle_significance(grid.reshape(b.n_curves, 1, -1))
+        mu, sd, rho = mu.cpu().numpy(), sd.cpu().numpy(), rho.cpu().numpy().astype(np.float64)
+        assert np.all(np.abs(mu - gm) <= 1e-6)
+        assert np.all(np.abs(sd - gs) <= 1e-4 * gs)
+        assert np.all(np.abs(rho - gr) <= 1e-3 * np.maximum(1.0, gr))
