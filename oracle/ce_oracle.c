@@ -211,7 +211,7 @@ static void cell_counts_from_bins(const double *t, const int32_t *mag_bins, int6
             counts[(int64_t)mag_bins[k] * n_phase + (j + n_phase - 1) % n_phase] += 1;
         double fr = y - floor(y);
         double d = fr < 1.0 - fr ? fr : 1.0 - fr;
-        d /= (double)n_phase;
+        if (!MUTANT(15)) d /= (double)n_phase;  /* 15: edge distance left in bin units */
         if (d < best) best = d;
     }
     if (dmin) *dmin = best;

@@ -92,6 +92,7 @@ def pin_fold_exact_rational(orc):
     # the batch path's epoch handling: a whole cell with t0 != 0 against exact bins
     bad_cells = 0
     cells = 0
+    worst_dmin = 0.0
     for trial in range(40):
         n_phase = int(rng.integers(2, 30))
         n_mag = int(rng.integers(1, 12))
@@ -107,8 +108,16 @@ def pin_fold_exact_rational(orc):
         cells += 1
         if not np.array_equal(counts, exact_counts):
             bad_cells += 1
+        # the edge distance the parity tests use: min over points of the exact phase's
+        # distance from a bin edge, in cycles (the fold's own rounding is ~1e-9 here)
+        ex = [exact_phase_scaled(Fraction(float(tk)) - Fraction(t0), period, pdot, n_phase)
+              for tk in t]
+        want = min(min(e - math.floor(e), math.floor(e) + 1 - e) for e in ex) / n_phase
+        worst_dmin = max(worst_dmin, abs(dmin - float(want)))
     out.append(("cell counts with epoch t0 match exact arithmetic",
                 bad_cells == 0 and cells >= 20, f"{bad_cells} of {cells} cells differ"))
+    out.append(("edge distance dmin matches exact arithmetic (cycles)", worst_dmin < 1e-8,
+                f"worst {worst_dmin:.3g}"))
     return out
 
 

@@ -2,7 +2,8 @@
 inverted log ratio, a transposed marginal, round instead of floor, a wrong
 magnitude scale, a wrong normaliser, a wrong epoch sign, a missing 1/P, one
 normalisation for all filters, the mean for the median, an overlapping bin
-dropped or not wrapped around the phase circle) must
+dropped or not wrapped around the phase circle, the edge distance in the
+wrong unit) must
 make at least one pin fail.  The mistakes are compiled into separate copies of
 the oracle on the CPU; the real oracle is untouched."""
 import numpy as np
@@ -25,6 +26,7 @@ MUTANTS = {
     12: "filter mean subtracted instead of its median",
     13: "overlapping bins: the second bin of each point dropped",
     14: "overlapping bins: no wrap-around from the first phase bin to the last",
+    15: "edge distance reported in phase bins instead of cycles",
 }
 
 
