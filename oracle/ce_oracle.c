@@ -20,6 +20,14 @@
  *   - Eq. 4 (Sec. 2.3): H_c = sum_ij p(m_i,phi_j) ln( p(phi_j) / p(m_i,phi_j) ).
  *   - Sec. 2.3 / Sec. 4: the detection is the grid minimum of H_c; its
  *     significance (Eq. 5) is computed from the grid in oracle/__init__.py.
+ *   - Sec. 2.3, options: half-overlapping neighbouring phase bins, and several
+ *     filters per source, each normalised by its own median and standard
+ *     deviation before the bins are taken.
+ *
+ * Every function is pinned by tests/oracle_pins.py to something other than
+ * itself: exact rational arithmetic on dyadic inputs, closed forms, library
+ * routines (scipy's Shannon entropy, numpy's median and standard deviation),
+ * brute force on tiny inputs and the paper's worked example (Fig. 2).
  *
  * Floating point: IEEE binary64, round-to-nearest, each operation written out
  * in a fixed order (build with -ffp-contract=off, never -ffast-math; the one
