@@ -110,7 +110,13 @@ typedef struct gce_handle_s *gce_handle;
 
 /* Create a handle on CUDA device `device` (it becomes current on the calling
  * thread).  The handle owns the device workspace, the autotune cache and the
- * captured CUDA graphs.  *h is NULL on failure. */
+ * captured CUDA graphs.  *h is NULL on failure.
+ * The workspace grows to the largest job seen and is kept until gce_destroy:
+ * 8 (FP64) or 16 bytes per point, 16 (FP64, SPLIT32) or 32 (FIXED32) bytes per
+ * (P, Pdot) trial, 8 k bytes per (curve, trial tile) for top-k (24 more with
+ * the significance), and 8 bytes per entry of the c ln c table (longest curve
+ * + 1).  A grid of 5,183,995 periods x 512 Pdot values thus holds 42 GB of
+ * trial constants in SPLIT32.  Growing a buffer waits for the device. */
 gce_status gce_create(gce_handle *h, int32_t device);
 
 /* Free everything the handle owns (waits for its outstanding work). */
