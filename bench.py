@@ -161,8 +161,10 @@ def oracle_rate(batch, seconds, n_threads=0):
                 batch.n_phase, batch.n_mag, n_threads=n_threads)
     dt = time.perf_counter() - t0
     used = orc.threads_used
-    desc = (f"{sample.n_curves} curves x {sample.periods.size} periods (every {stride}th) x "
-            f"{sample.pdots.size} Pdot = {sample.point_trials:.3g} point-trials in {dt:.1f} s")
+    which = "all" if stride == 1 else f"a stride-{stride} subset"
+    desc = (f"first {sample.n_curves} curves x {sample.periods.size} periods ({which} of "
+            f"{batch.periods.size}) x {sample.pdots.size} Pdot = {sample.point_trials:.3g} "
+            f"point-trials in {dt:.1f} s")
     return sample.point_trials / dt, used, desc
 
 
