@@ -21,3 +21,18 @@ def test_reference_arm_json_line():
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"]
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"],
                            "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_pdot_override_applies_to_pdot_workloads_only(monkeypatch):
+    """--pdots resizes the Pdot axis of the workloads that have one (Sec. 3 runs 32,
+    128 and 512 values) and is refused for the others."""
+    import pytest
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--workload", "5", "--pdots", "128"])
+    assert bench.workload_overrides(bench.parse()) == {"n_pdots": 128}
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--workload", "1"])
+    assert bench.workload_overrides(bench.parse()) == {}
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--workload", "1", "--pdots", "8"])
+    with pytest.raises(SystemExit):
+        bench.workload_overrides(bench.parse())
