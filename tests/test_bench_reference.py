@@ -5,6 +5,8 @@ import os
 import subprocess
 import sys
 
+import pytest
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -26,7 +28,6 @@ def test_reference_arm_json_line():
 def test_pdot_override_applies_to_pdot_workloads_only(monkeypatch):
     """--pdots resizes the Pdot axis of the workloads that have one (Sec. 3 runs 32,
     128 and 512 values) and is refused for the others."""
-    import pytest
     sys.path.insert(0, ROOT)
     import bench
     monkeypatch.setattr(sys, "argv", ["bench.py", "--workload", "5", "--pdots", "128"])
