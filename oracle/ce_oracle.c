@@ -313,6 +313,7 @@ int oracle_ce_cells(const double *times, const double *mags, const int64_t *offs
         int64_t c = cell_curve[k];
         int64_t p = cell_trial[k] % n_periods, q = cell_trial[k] / n_periods;
         int64_t lo = offsets[c], n = offsets[c + 1] - offsets[c];
+        if (MUTANT(16) && c > 0) lo = offsets[c - 1];  /* 16: the previous curve's start */
         int64_t *cnt = out_counts ? out_counts + k * (int64_t)n_mag * n_phase : NULL;
         double dmin;
         out_H[k] = oracle_cell(times + lo, mags + lo, n, t0, periods[p], pdots[q],

@@ -565,12 +565,52 @@ def pin_selection(orc):
     return out
 
 
+def pin_batch_paths(orc):
+    """The batch paths against the single-cell path (itself pinned to exact
+    arithmetic above): on a ragged batch with t0 != 0 and several Pdot values, the
+    full grid (any thread count) and the sampled cells (with their counts) equal
+    cell() at every (curve, q, p), with plain and overlapping bins, so curve
+    offsets and the flat index q * n_periods + p are taken right."""
+    rng = np.random.default_rng(59)
+    lengths = [1, 2, 17, 64, 130]
+    t = np.concatenate([np.sort(rng.uniform(0, 5e7, n)) for n in lengths])
+    m = rng.normal(15, 0.3, t.size)
+    offs = np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64)
+    periods = np.exp(rng.uniform(np.log(300), np.log(3000), 23))
+    pdots = np.array([0.0, -4e-11, 2e-11])
+    t0 = 1.25e7
+    n_p, n_q, n_c = periods.size, pdots.size, len(lengths)
+    out = []
+    for overlap in (False, True):
+        grid = orc.ce_grid(t, m, offs, periods, pdots, 9, 7, t0=t0, n_threads=1,
+                           overlap=overlap)
+        grid4 = orc.ce_grid(t, m, offs, periods, pdots, 9, 7, t0=t0, n_threads=4,
+                            overlap=overlap)
+        cc = np.repeat(np.arange(n_c), n_p * n_q)
+        ct = np.tile(np.arange(n_p * n_q), n_c)
+        hc, _, counts = orc.ce_cells(t, m, offs, periods, pdots, 9, 7, cc, ct, t0=t0,
+                                     with_counts=True, overlap=overlap)
+        ok = np.array_equal(grid, grid4)
+        ok &= np.array_equal(hc, grid.reshape(-1))
+        for c in range(n_c):
+            tc, mc = t[offs[c]:offs[c + 1]], m[offs[c]:offs[c + 1]]
+            for q in range(n_q):
+                for p_ in range(n_p):
+                    h1, c1, _ = orc.cell(tc, mc, t0, periods[p_], pdots[q], 9, 7,
+                                         overlap=overlap)
+                    k = (c * n_q + q) * n_p + p_
+                    ok &= h1 == grid[c, q, p_] and np.array_equal(c1, counts[k])
+        out.append((f"batch grid and sampled cells equal the single-cell path"
+                    f"{' (overlapping bins)' if overlap else ''}", bool(ok), ""))
+    return out
+
+
 ALL_PINS = (
     pin_fold_exact_rational, pin_fold_edges, pin_pdot_zero_plain_fold, pin_eq6_dephasing,
     pin_mag_bins, pin_entropy_chain_rule, pin_entropy_special_cases,
     pin_entropy_bounds_and_invariance, pin_brute_force_tiny, pin_paper_worked_example,
     pin_recovery, pin_overlapping_bins, pin_significance, pin_band_normalization,
-    pin_selection,
+    pin_selection, pin_batch_paths,
 )
 
 

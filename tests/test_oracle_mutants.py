@@ -3,7 +3,7 @@ inverted log ratio, a transposed marginal, round instead of floor, a wrong
 magnitude scale, a wrong normaliser, a wrong epoch sign, a missing 1/P, one
 normalisation for all filters, the mean for the median, an overlapping bin
 dropped or not wrapped around the phase circle, the edge distance in the
-wrong unit) must
+wrong unit, a sampled cell read from the wrong curve) must
 make at least one pin fail.  The mistakes are compiled into separate copies of
 the oracle on the CPU; the real oracle is untouched."""
 import numpy as np
@@ -27,6 +27,7 @@ MUTANTS = {
     13: "overlapping bins: the second bin of each point dropped",
     14: "overlapping bins: no wrap-around from the first phase bin to the last",
     15: "edge distance reported in phase bins instead of cycles",
+    16: "sampled cells read from the previous curve's first point",
 }
 
 
