@@ -269,6 +269,15 @@ gce_status gce_stream_status(gce_handle h, void *stream);
  * around that launch.  Waits for the events. */
 gce_status gce_kernel_time(gce_handle h, float *ms);
 
+/* Number of CUDA kernels the last search call on this handle launched, directly
+ * or inside its CUDA graph: the checks, trial constants, preparation (plus the
+ * per-filter statistics with multi-filter input), the CE kernel and the top-k
+ * merge (two levels when a curve has more than 4096 tile candidates), one
+ * launch per curve for gce_ce_grid_single, and the c ln c table when a call
+ * extended it.  0 before any call and after a call on an empty batch.
+ * Host-side only: no device work, no wait. */
+gce_status gce_last_launches(gce_handle h, int32_t *n);
+
 /* Time candidate launch shapes on a synthetic job of the given size and keep
  * the fastest for (phase mode, bins, curve-length bucket) in the handle's
  * cache; later calls with a matching key use it.  Jobs with a Pdot axis

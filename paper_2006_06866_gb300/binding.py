@@ -74,6 +74,7 @@ SIGNATURES = {
                              _P]),
     "gce_stream_status": (_I32, [_P, _P]),
     "gce_kernel_time": (_I32, [_P, ctypes.POINTER(ctypes.c_float)]),
+    "gce_last_launches": (_I32, [_P, ctypes.POINTER(ctypes.c_int32)]),
     "gce_autotune": (_I32, [_P, _CFG, _I32, _I64]),
     "gce_autotune_job": (_I32, [_P, _P, _P, _HOFF, _I32, _P, _I32, _P, _I32, _CFG]),
     "gce_get_tuning": (_I32, [_P, _CFG, _I32, _I32, _TUN]),
@@ -391,6 +392,13 @@ def gce_kernel_time(handle: Handle) -> float:
     ms = ctypes.c_float()
     _check(lib().gce_kernel_time(handle.ptr, ctypes.byref(ms)), handle.ptr)
     return float(ms.value)
+
+
+def gce_last_launches(handle: Handle) -> int:
+    """Kernels the last search call on this handle launched (directly or in its graph)."""
+    n = ctypes.c_int32()
+    _check(lib().gce_last_launches(handle.ptr, ctypes.byref(n)), handle.ptr)
+    return int(n.value)
 
 
 def gce_autotune(handle: Handle, cfg: Config, n_obs_hint: int, n_trials_hint: int):

@@ -62,6 +62,7 @@ struct gce_handle_s {
     bool staged_pending = false;
     cudaEvent_t k0 = nullptr, k1 = nullptr;  // around the CE kernel (GCE_FLAG_TIME_KERNEL)
     bool timed = false;
+    int launches = 0;                    // kernels the last job launched (directly or in its graph)
     std::map<TuneKey, gce_tuning> tune;
     std::map<GraphKey, cudaGraphExec_t> graphs;
 };
@@ -379,9 +380,11 @@ gce_status enqueue(gce_handle h, const Job &j, const Plan &pl, cudaStream_t s, b
                                 cudaMemcpyHostToDevice, s));
     CUDA_TRY(h, cudaMemcpyAsync(h->order.p, h->h_order, sizeof(int) * j.n_curves,
                                 cudaMemcpyHostToDevice, s));
+    int n_launch = 0;  // kernels this sequence launches, for gce_last_launches
     CUDA_TRY(h, launch_init(st, s));
     CUDA_TRY(h, launch_scan(j.times, j.mags, pl.n_points, j.periods, j.n_periods, j.pdots,
                             j.n_pdots, cfg->t0, st, s));
+    n_launch += 2;
     TrialArgs ta;
     ta.periods = j.periods;
     ta.pdots = j.pdots;
@@ -390,6 +393,7 @@ gce_status enqueue(gce_handle h, const Job &j, const Plan &pl, cudaStream_t s, b
     ta.trialc = h->trialc.p;
     ta.state = st;
     CUDA_TRY(h, launch_trials(mode, ta, s));
+    ++n_launch;
     PrepArgs pa;
     pa.times = j.times;
     pa.mags = j.mags;
@@ -403,10 +407,13 @@ gce_status enqueue(gce_handle h, const Job &j, const Plan &pl, cudaStream_t s, b
     pa.bands = j.bands;
     pa.band_stats = (const double2 *)h->band_stats.p;
     pa.n_bands = j.bands ? j.n_bands : 0;
-    if (j.bands)
+    if (j.bands) {
         CUDA_TRY(h, launch_band_stats(j.mags, j.bands, pa.offsets, j.n_curves, j.n_bands,
                                       (double2 *)h->band_stats.p, st, s));
+        ++n_launch;
+    }
     CUDA_TRY(h, launch_prep(mode, pa, s));
+    ++n_launch;
     MainArgs ma;
     ma.payload = h->payload.p;
     ma.offsets = (const long long *)h->offsets.p;
@@ -440,6 +447,7 @@ gce_status enqueue(gce_handle h, const Job &j, const Plan &pl, cudaStream_t s, b
             ma.out = j.out;
             if (timed && (ms = mark(h, h->k0, s, capturing)) != GCE_OK) return ms;
             CUDA_TRY(h, launch_main(mode, pl.tpt, pl.block, pl.grid, pl.smem, ma, s));
+            ++n_launch;
             if (timed && (ms = mark(h, h->k1, s, capturing)) != GCE_OK) return ms;
             break;
         case JOB_TOPK:
@@ -448,6 +456,7 @@ gce_status enqueue(gce_handle h, const Job &j, const Plan &pl, cudaStream_t s, b
             if (j.rho) ma.stats = (TileStats *)h->stats.p;
             if (timed && (ms = mark(h, h->k0, s, capturing)) != GCE_OK) return ms;
             CUDA_TRY(h, launch_main(mode, pl.tpt, pl.block, pl.grid, pl.smem, ma, s));
+            ++n_launch;
             if (timed && (ms = mark(h, h->k1, s, capturing)) != GCE_OK) return ms;
             if (pl.n_groups > 0) {
                 // many tiles per curve: reduce groups of tiles first, then merge the groups
@@ -459,16 +468,19 @@ gce_status enqueue(gce_handle h, const Job &j, const Plan &pl, cudaStream_t s, b
                 CUDA_TRY(h, launch_topk_merge((const unsigned long long *)h->cand2.p, j.n_curves,
                                               pl.n_groups, j.k, j.topk_H, (long long *)j.topk_idx,
                                               stats2, j.mean, j.std_dev, j.rho, st, s));
+                n_launch += 2;
             } else {
                 CUDA_TRY(h, launch_topk_merge((const unsigned long long *)h->cand.p, j.n_curves,
                                               pl.n_tiles, j.k, j.topk_H, (long long *)j.topk_idx,
                                               ma.stats, j.mean, j.std_dev, j.rho, st, s));
+                ++n_launch;
             }
             break;
         case JOB_SINGLE:
             ma.out = j.out;
             if (timed && (ms = mark(h, h->k0, s, capturing)) != GCE_OK) return ms;
             for (int c = 0; c < j.n_curves; ++c) CUDA_TRY(h, launch_single(ma, c, 0, s));
+            n_launch += j.n_curves;
             if (timed && (ms = mark(h, h->k1, s, capturing)) != GCE_OK) return ms;
             break;
         case JOB_COUNTS:
@@ -477,13 +489,16 @@ gce_status enqueue(gce_handle h, const Job &j, const Plan &pl, cudaStream_t s, b
                                             cfg->n_phase_bins, s));
             CUDA_TRY(h, launch_counts(mode, ma, j.n_cells, (const long long *)j.cell_curve,
                                       (const long long *)j.cell_trial, (unsigned int *)j.counts, s));
+            if (j.n_cells > 0) ++n_launch;
             break;
     }
+    h->launches += n_launch;
     return GCE_OK;
 }
 
 gce_status run_job(gce_handle h, const Job &j, cudaStream_t s) {
     if (!h) return GCE_ERR_INVALID;
+    h->launches = 0;
     const gce_status chk = gce_check_job(j.h_offsets, j.n_curves, j.n_periods, j.n_pdots, j.cfg,
                                          j.kind == JOB_TOPK ? j.k : 0);
     if (chk != GCE_OK) return fail(h, chk, "argument check failed");
@@ -534,6 +549,7 @@ gce_status run_job(gce_handle h, const Job &j, cudaStream_t s) {
     if (pl.n_max > h->table_n) {
         if ((st = ensure(h, h->table, 8 * (size_t)(pl.n_max + 1))) != GCE_OK) return st;
         CUDA_TRY(h, launch_table((unsigned long long *)h->table.p, pl.n_max, s));
+        ++h->launches;
         h->table_n = pl.n_max;
     }
 
@@ -790,6 +806,12 @@ extern "C" gce_status gce_kernel_time(gce_handle h, float *ms) {
     if (!h->timed) return fail(h, GCE_ERR_INVALID, "the last call was not made with GCE_FLAG_TIME_KERNEL");
     CUDA_TRY(h, cudaEventSynchronize(h->k1));
     CUDA_TRY(h, cudaEventElapsedTime(ms, h->k0, h->k1));
+    return GCE_OK;
+}
+
+extern "C" gce_status gce_last_launches(gce_handle h, int32_t *n) {
+    if (!h || !n) return GCE_ERR_INVALID;
+    *n = h->launches;
     return GCE_OK;
 }
 

@@ -312,3 +312,35 @@ def test_topk_two_level_merge(h, mode):
         assert np.all(np.abs(mu - gm) <= 1e-6)
         assert np.all(np.abs(sd - gs) <= 1e-4 * gs)
         assert np.all(np.abs(rho - gr) <= 1e-3 * np.maximum(1.0, gr))
+
+
+def test_launch_count():
+    """gce_last_launches counts the kernels of the last call: checks, scan, trial
+    constants, preparation, the CE kernel, then the top-k merge (two levels on
+    grids with many tiles per curve); the c ln c table once per handle; one launch
+    per curve for the single-launch baseline; nothing for an empty batch."""
+    hh = g.Handle(0)
+    try:
+        b = small_batch(seed=12, n_curves=3, n_obs=120, n_periods=300)
+        args = dev_args(b)
+        cfg = g.Config(15, 10, "split32")
+        g.gce_ce_topk(hh, cfg=cfg, k=5, **args)
+        assert g.gce_last_launches(hh) == 7  # + the c ln c table, built by the first call
+        g.gce_ce_topk(hh, cfg=cfg, k=5, **args)
+        assert g.gce_last_launches(hh) == 6
+        g.gce_ce_grid(hh, cfg=cfg, **args)
+        assert g.gce_last_launches(hh) == 5
+        g.gce_ce_grid_single(hh, cfg=g.Config(15, 10, "fp64"), **args)
+        assert g.gce_last_launches(hh) == 4 + b.n_curves
+        big = dev_args(small_batch(seed=12, n_curves=3, n_obs=120, n_periods=2_000_000))
+        g.gce_ce_detect(hh, cfg=cfg, k=5, **big)
+        assert g.gce_last_launches(hh) == 7  # the merge's first level over groups of tiles
+        bands = torch.zeros(b.times.size, dtype=torch.uint8, device="cuda")
+        g.gce_ce_grid_bands(hh, bands=bands, n_bands=1, cfg=cfg, **args)
+        assert g.gce_last_launches(hh) == 6  # + the per-filter statistics
+        empty = dict(args, offsets=np.zeros(1, dtype=np.int64))
+        g.gce_ce_topk(hh, cfg=cfg, k=1, **empty)
+        assert g.gce_last_launches(hh) == 0
+        assert g.gce_stream_status(hh) == g.GCE_OK
+    finally:
+        hh.close()
