@@ -37,3 +37,14 @@ def test_pdot_override_applies_to_pdot_workloads_only(monkeypatch):
     monkeypatch.setattr(sys, "argv", ["bench.py", "--workload", "1", "--pdots", "8"])
     with pytest.raises(SystemExit):
         bench.workload_overrides(bench.parse())
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    """Under torchrun only rank 0 runs the reference arm; the other ranks exit 0
+    without work or output."""
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--gpus", "2", "--steps", "1", "--warmup", "1", "--ref-seconds", "2"],
+                       capture_output=True, text=True, timeout=120, cwd=ROOT, env=env)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip() == ""
