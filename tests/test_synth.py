@@ -97,3 +97,21 @@ def test_paper_workload():
     assert np.all(b.truth_pdot < 0)
     gaps = np.diff(b.curve(0)[0]) / DAY
     assert 6.5 < gaps.mean() < 7.5
+
+
+def test_multiband_generator():
+    """Multi-filter stand-in: one filter index per visit, each filter present, the
+    same seed gives the same bytes, and the filters of a curve differ by their
+    colour offsets (so normalising each filter on its own matters)."""
+    b, bands = synth.make_multiband(5, n_curves=6, n_obs=400, n_bands=3)
+    b2, bands2 = synth.make_multiband(5, n_curves=6, n_obs=400, n_bands=3)
+    assert np.array_equal(b.times, b2.times) and np.array_equal(bands, bands2)
+    assert bands.dtype == np.uint8 and bands.shape == b.times.shape and bands.max() < 3
+    spread = []
+    for c in range(b.n_curves):
+        lo, hi = b.offsets[c], b.offsets[c + 1]
+        assert hi - lo >= 300
+        assert np.all(np.diff(b.times[lo:hi]) >= 0)
+        meds = [np.median(b.mags[lo:hi][bands[lo:hi] == k]) for k in range(3)]
+        spread.append(max(meds) - min(meds))
+    assert np.median(spread) > 0.1
