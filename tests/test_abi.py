@@ -92,8 +92,8 @@ def test_check_job_rejects(L, case):
     assert _ok(**case) == g.GCE_ERR_INVALID
 
 
-def test_loading_fails_loudly_without_the_library(monkeypatch, tmp_path):
-    monkeypatch.setattr(binding, "LIB_PATH", str(tmp_path / "missing.so"))
+def test_loading_fails_loudly_without_the_library(monkeypatch):
+    monkeypatch.setattr(binding, "LIB_PATH", os.path.join(ROOT, "no-such-dir", "missing.so"))
     monkeypatch.setattr(binding, "_lib", None)
     with pytest.raises(RuntimeError, match="missing"):
         binding.lib()
