@@ -249,8 +249,12 @@ double oracle_cell(const double *t, const double *m, int64_t n, double t0,
  *   times, mags: concatenated curves; curve c owns [offsets[c], offsets[c+1]).
  *   out_H[(c * n_pdots + q) * n_periods + p] = H of curve c at (periods[p], pdots[q]).
  *   out_dmin: same layout, nullable.
- *   n_threads: OpenMP threads over (curve, pdot) rows (<= 0: the runtime default).
+ *   n_threads: OpenMP threads (<= 0: the runtime default).  The threads share
+ *   out rows of (curve, pdot, run of ORACLE_PERIOD_RUN periods), so that a
+ *   small batch still keeps every thread busy; each cell is computed exactly
+ *   as by oracle_cell, whatever the split.
  * Returns the number of threads used. */
+#define ORACLE_PERIOD_RUN 64
 int oracle_ce_grid(const double *times, const double *mags, const int64_t *offsets,
                    int32_t n_curves, const double *periods, int32_t n_periods,
                    const double *pdots, int32_t n_pdots, int32_t n_phase, int32_t n_mag,
@@ -258,7 +262,8 @@ int oracle_ce_grid(const double *times, const double *mags, const int64_t *offse
                    int32_t n_threads)
 {
     int used = 1;
-    int64_t rows = (int64_t)n_curves * n_pdots;
+    const int64_t runs = ((int64_t)n_periods + ORACLE_PERIOD_RUN - 1) / ORACLE_PERIOD_RUN;
+    const int64_t rows = (int64_t)n_curves * n_pdots * runs;
 #ifdef _OPENMP
     if (n_threads > 0) omp_set_num_threads(n_threads);
 #pragma omp parallel
@@ -269,18 +274,21 @@ int oracle_ce_grid(const double *times, const double *mags, const int64_t *offse
 #pragma omp parallel for schedule(dynamic, 1)
 #endif
     for (int64_t r = 0; r < rows; ++r) {
-        int32_t c = (int32_t)(r / n_pdots);
-        int32_t q = (int32_t)(r % n_pdots);
+        const int64_t cq = r / runs;  /* curve * n_pdots + pdot */
+        int32_t c = (int32_t)(cq / n_pdots);
+        int32_t q = (int32_t)(cq % n_pdots);
+        int32_t p0 = (int32_t)((r % runs) * ORACLE_PERIOD_RUN);
+        int32_t p1 = p0 + ORACLE_PERIOD_RUN < n_periods ? p0 + ORACLE_PERIOD_RUN : n_periods;
         int64_t lo = offsets[c], n = offsets[c + 1] - offsets[c];
         int32_t *bins = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
         int64_t *counts = (int64_t *)malloc(sizeof(int64_t) * (size_t)n_mag * (size_t)n_phase);
         oracle_mag_bins(mags + lo, n, n_mag, bins);
-        for (int32_t p = 0; p < n_periods; ++p) {
+        for (int32_t p = p0; p < p1; ++p) {
             double f, a, dmin;
             oracle_trial_constants(periods[p], pdots[q], &f, &a);
             cell_counts_from_bins(times + lo, bins, n, t0, f, a, n_phase, n_mag, overlap, counts,
                                   &dmin);
-            int64_t o = r * n_periods + p;
+            int64_t o = cq * n_periods + p;
             out_H[o] = oracle_entropy(counts, n_mag, n_phase);
             if (out_dmin) out_dmin[o] = dmin;
         }
