@@ -47,8 +47,6 @@ FOLD_OPS = {"split32": (6, 15), "fixed32": (5, 8), "fp64": (5, 7)}
 ISSUE_LANES = 128
 FP32_LANES = 128
 FP64_LANES = 2
-SM_COUNT = 152
-SM_MAX_MHZ = 2070.0
 
 
 def parse():
@@ -135,37 +133,156 @@ def cpu_model():
 
 # ---------------------------------------------------------------- oracle leg
 
-def oracle_rate(batch, seconds, n_threads=0):
-    """The CPU oracle on a bounded sample of the workload: the first curves x a
-    strided subset of the periods, sized to take about `seconds`.  Returns
-    (point-trials/s, threads, sample description)."""
+def _oracle_sample(batch, pt_want, min_curves):
+    """The first curves of the workload x a strided subset of its periods x all
+    its Pdot values, holding about pt_want point-trials."""
+    n_obs = float(np.mean(batch.n_obs))
+    per_curve = n_obs * batch.periods.size * batch.pdots.size
+    n_curves = int(min(batch.n_curves, max(min_curves, int(np.ceil(pt_want / per_curve)))))
+    n_periods = int(min(batch.periods.size,
+                        max(64, pt_want / (n_curves * n_obs * batch.pdots.size))))
+    stride = max(1, batch.periods.size // n_periods)
+    return batch.subset(list(range(n_curves)), periods=batch.periods[::stride]), stride
+
+
+def _describe(sample, batch, stride, dt, threads):
+    which = "all" if stride == 1 else f"a stride-{stride} subset"
+    return (f"first {sample.n_curves} curves x {sample.periods.size} periods ({which} of "
+            f"{batch.periods.size}) x {sample.pdots.size} Pdot = {sample.point_trials:.3g} "
+            f"point-trials in {dt:.2f} s on {threads} thread{'s' if threads > 1 else ''}")
+
+
+def oracle_rate(batch, seconds, n_threads=0, overlap=False, keep=False, single=True):
+    """The CPU oracle on bounded samples of the workload: one thread for about a
+    fifth of `seconds` (at most 4 s), then all `n_threads` threads for about
+    `seconds`.  The oracle splits its grid into (curve, Pdot, run of 64
+    periods) rows, so a sample of a few curves still keeps every thread busy.
+    Returns a dict (point-trials/s on all threads and on one, the threads used,
+    the samples) and, with keep, the all-thread sample with its oracle grid and
+    edge distances (the parity block reuses them)."""
     import oracle
     orc = oracle.Oracle()
-    n_obs = int(batch.n_obs[0])
-    # calibration run: one curve x 200 periods
-    cal = batch.subset([0], periods=batch.periods[:: max(1, batch.periods.size // 200)])
-    t0 = time.perf_counter()
-    orc.ce_grid(cal.times, cal.mags, cal.offsets, cal.periods, cal.pdots, batch.n_phase,
-                batch.n_mag, n_threads=1)
-    dt = max(time.perf_counter() - t0, 1e-4)
-    rate1 = cal.point_trials / dt
-    threads = os.cpu_count() or 1
-    want = rate1 * threads * seconds  # point-trials the sample should hold
-    per_curve = n_obs * batch.periods.size * batch.pdots.size
-    n_curves = int(min(batch.n_curves, max(threads, int(np.ceil(want / per_curve)))))
-    n_periods = int(min(batch.periods.size, max(64, want / (n_curves * n_obs * batch.pdots.size))))
-    stride = max(1, batch.periods.size // n_periods)
-    sample = batch.subset(list(range(n_curves)), periods=batch.periods[::stride])
-    t0 = time.perf_counter()
-    orc.ce_grid(sample.times, sample.mags, sample.offsets, sample.periods, sample.pdots,
-                batch.n_phase, batch.n_mag, n_threads=n_threads)
-    dt = time.perf_counter() - t0
+    threads = n_threads or os.cpu_count() or 1
+
+    def run(sample, nt):
+        t0 = time.perf_counter()
+        out = orc.ce_grid(sample.times, sample.mags, sample.offsets, sample.periods, sample.pdots,
+                          batch.n_phase, batch.n_mag, t0=batch.t0, n_threads=nt, with_dmin=True,
+                          overlap=overlap)
+        return out, time.perf_counter() - t0
+
+    # calibration: one curve x about 200 periods on one thread
+    cal = batch.subset([0], periods=batch.periods[:: max(1, batch.periods.size // 200)],
+                       pdots=batch.pdots[:1])
+    _, dt = run(cal, 1)
+    rate1 = cal.point_trials / max(dt, 1e-4)
+    res = {}
+    if single:
+        one, s1 = _oracle_sample(batch, rate1 * min(4.0, max(0.5, seconds / 5)), 1)
+        _, dt1 = run(one, 1)
+        rate1 = one.point_trials / dt1
+        res = {"single_thread_value": rate1,
+               "single_thread_sample": _describe(one, batch, s1, dt1, 1)}
+    sample, stride = _oracle_sample(batch, rate1 * threads * seconds, 1)
+    (ref, dmin), dt = run(sample, threads)
     used = orc.threads_used
-    which = "all" if stride == 1 else f"a stride-{stride} subset"
-    desc = (f"first {sample.n_curves} curves x {sample.periods.size} periods ({which} of "
-            f"{batch.periods.size}) x {sample.pdots.size} Pdot = {sample.point_trials:.3g} "
-            f"point-trials in {dt:.1f} s")
-    return sample.point_trials / dt, used, desc
+    res = {"value": sample.point_trials / dt, "unit": UNIT, "cores": used, "kind": "oracle",
+           "sample": _describe(sample, batch, stride, dt, used), **res}
+    return (res, (sample, ref, dmin)) if keep else (res, None)
+
+
+def oracle_c1_full(n_threads):
+    """The small single-curve configuration (workload 0: one 100-point curve x
+    1000 periods, 15 x 10 bins) in full on the oracle: median of five runs."""
+    import oracle
+    import synth
+    orc = oracle.Oracle()
+    b = synth.make_config(0)
+    out = {}
+    for nt, key in ((1, "single_thread_s"), (n_threads, "all_threads_s")):
+        ts = []
+        for _ in range(5):
+            t0 = time.perf_counter()
+            orc.ce_grid(b.times, b.mags, b.offsets, b.periods, b.pdots, b.n_phase, b.n_mag,
+                        n_threads=nt)
+            ts.append(time.perf_counter() - t0)
+        out[key] = float(np.median(ts))
+    out["point_trials"] = int(b.point_trials)
+    out["threads"] = int(n_threads)
+    return out
+
+
+# Parity contract of the GPU folds against the oracle: |dH| bound per fold, and
+# the fold's phase-error bound eps in cycles (cells whose points all lie farther
+# than 4 eps from a phase-bin edge are held to the |dH| bound; 0 = every cell).
+PARITY_TOL = {"fp64": 1e-6, "split32": 1e-4, "fixed32": 1e-4}
+PARITY_EPS = {"fp64": 0.0, "split32": 2.5e-7, "fixed32": 4e-9}
+
+
+def parity_block(g, h, dev, stream, sample, ref, dmin, overlap, n_count_cells=2000):
+    """Per fold: CE error and argmin agreement of the device grid against the
+    oracle grid of the CPU-baseline sample, and exact-count agreement on seeded
+    sampled cells (gce_ce_counts against the oracle's counts)."""
+    import torch
+    nc = sample.n_curves
+    flat, dm = ref.reshape(nc, -1), dmin.reshape(nc, -1)
+    args = dict(times=torch.tensor(sample.times, device=dev),
+                mags=torch.tensor(sample.mags, device=dev),
+                offsets=np.asarray(sample.offsets, dtype=np.int64),
+                periods=torch.tensor(sample.periods, device=dev),
+                pdots=torch.tensor(sample.pdots, device=dev))
+    rng = np.random.default_rng(20200611)
+    n_trials = flat.shape[1]
+    cc = rng.integers(0, nc, size=n_count_cells).astype(np.int64)
+    ct = rng.integers(0, n_trials, size=n_count_cells).astype(np.int64)
+    import oracle
+    _, cdmin, rcounts = oracle.Oracle().ce_cells(
+        sample.times, sample.mags, sample.offsets, sample.periods, sample.pdots, sample.n_phase,
+        sample.n_mag, cc, ct, t0=sample.t0, with_counts=True, overlap=overlap)
+    # the oracle's best and runner-up cell per curve (ties: the smaller flat index)
+    best = flat.argmin(axis=1)
+    masked = flat.copy()
+    masked[np.arange(nc), best] = np.inf
+    second = masked.argmin(axis=1) if flat.shape[1] > 1 else best
+    del masked
+    out = {"cells": int(flat.size), "curves": nc, "count_cells": n_count_cells}
+    with torch.cuda.stream(stream):
+        for mode in ("fp64", "split32", "fixed32"):
+            cfg = g.Config(sample.n_phase, sample.n_mag, mode, t0=sample.t0, overlap=overlap)
+            got = g.gce_ce_grid(h, cfg=cfg, stream=stream, **args)
+            cnt = g.gce_ce_counts(h, cfg=cfg, cell_curve=torch.tensor(cc, device=dev),
+                                  cell_trial=torch.tensor(ct, device=dev), stream=stream, **args)
+            if g.gce_stream_status(h, stream) != g.GCE_OK:
+                out[mode] = {"error": "device input check failed"}
+                continue
+            got = got.cpu().numpy().astype(np.float64).reshape(nc, -1)
+            cnt = cnt.cpu().numpy().astype(np.int64)
+            err = np.abs(got - flat)
+            near = dm <= 4 * PARITY_EPS[mode]
+            agree = ambiguous = 0
+            dev_best = got.argmin(axis=1)  # first occurrence: ties to the smaller index
+            for c in range(nc):
+                b, s2 = best[c], second[c]
+                if (s2 != b and flat[c, s2] - flat[c, b] <= 1e-4) or near[c, b]:
+                    ambiguous += 1
+                    continue
+                agree += int(dev_best[c] == b)
+            cfar = cdmin > 4 * PARITY_EPS[mode]
+            same = np.all(cnt == rcounts, axis=(1, 2))
+            out[mode] = {
+                "tol": PARITY_TOL[mode], "eps_cycles": PARITY_EPS[mode],
+                "max_abs_dH": float(err.max()),
+                "max_abs_dH_off_edge": float(err[~near].max()) if (~near).any() else 0.0,
+                "near_edge_frac": float(near.mean()),
+                "argmin_agree": agree, "argmin_decided": nc - ambiguous,
+                "argmin_tie_ambiguous": ambiguous,
+                "counts_exact": int(same.sum()), "counts_exact_off_edge": int(same[cfar].sum()),
+                "count_cells_off_edge": int(cfar.sum()),
+                "pass": bool(err[~near].max() <= PARITY_TOL[mode] if (~near).any() else True)
+                and agree == nc - ambiguous
+                and (mode != "fp64" or bool(same.all())),
+            }
+    return out
 
 
 def run_reference(args, rank, world):
@@ -174,25 +291,32 @@ def run_reference(args, rank, world):
         return
     import synth
     batch = synth.make_config(args.workload, **workload_overrides(args))
+    if args.phase_bins:
+        batch.n_phase = int(args.phase_bins)
     per_step = max(0.5, args.ref_seconds / max(1, args.steps + args.warmup))
+    threads = os.cpu_count() or 1
     rates = []
-    used = 1
-    desc = ""
+    info = single = None
     for s in range(args.warmup + args.steps):
-        r, used, desc = oracle_rate(batch, per_step, n_threads=os.cpu_count() or 1)
+        info, _ = oracle_rate(batch, per_step, n_threads=threads, overlap=bool(args.overlap),
+                              single=single is None)
+        if single is None:  # the one-thread rate, measured once
+            single = {k: v for k, v in info.items() if k.startswith("single_thread")}
         if s >= args.warmup:
-            rates.append(r)
+            rates.append(info["value"])
     value = float(np.median(rates))
+    cpu = dict(info, value=value, **single)
+    cpu["sample"] = f"median over {len(rates)} steps, each {info['sample']}"
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
         "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"{synth.CONFIG_NAMES[args.workload]}: {batch.n_curves} curves, "
                                f"{batch.periods.size} periods x {batch.pdots.size} Pdot, "
-                               f"{batch.n_phase}x{batch.n_mag} bins",
+                               f"{batch.n_phase}x{batch.n_mag} bins"
+                               + (", 50 % overlapping" if args.overlap else ""),
                    "cpu": cpu_model()},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle",
-                         "sample": desc},
+        "cpu_baseline": cpu,
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -247,6 +371,17 @@ class ClockSampler:
         return {"sm_mhz": float(np.median(sm)) if sm else None,
                 "sm_max_mhz": float(max(smax)) if smax else None,
                 "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def query_max_sm_mhz(device_index):
+    """The device's maximum SM clock from nvidia-smi (MHz), or None."""
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", str(device_index),
+                              "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits"],
+                             capture_output=True, text=True, timeout=30).stdout
+        return float(out.strip().splitlines()[0])
+    except Exception:
+        return None
 
 
 # ---------------------------------------------------------------- GPU leg
@@ -453,21 +588,35 @@ def main():
                 value / world / extras["fp64_single_launch"]["value"])
 
     cpu = None
+    parity = None
     if rank == 0 and world == 1 and not args.no_cpu:
         try:
-            r, used, desc = oracle_rate(batch, args.cpu_seconds, n_threads=os.cpu_count() or 1)
-            cpu = {"value": r, "unit": UNIT, "cores": used, "kind": "oracle", "sample": desc,
-                   "cpu": cpu_model()}
+            threads = os.cpu_count() or 1
+            cpu, kept = oracle_rate(batch, args.cpu_seconds, n_threads=threads, overlap=ovl,
+                                    keep=not nb)
+            cpu["cpu"] = cpu_model()
+            cpu["plain_single_curve_full"] = oracle_c1_full(threads)
         except Exception as e:  # the baseline is context; never fail the bench on it
             cpu = {"value": None, "unit": UNIT, "cores": 0, "kind": "oracle",
                    "sample": f"unavailable: {e}"}
+            kept = None
+        if kept is not None:
+            # per-fold CE error and argmin agreement against the oracle, on the
+            # grid the oracle has just computed for the baseline
+            parity = parity_block(g, h, dev, stream, *kept, overlap=ovl)
+            parity["sample"] = cpu["sample"]
 
     roof = None
     if kern_ms:
         has_pdot = bool(np.any(batch.pdots != 0.0))
         fold = FOLD_OPS[args.mode][1 if has_pdot else 0]
         rate = pt_step / (kern_ms / 1e3)
-        clk = SM_COUNT * SM_MAX_MHZ * 1e6
+        # the peak's SM count and maximum SM clock are the device's own: the SM
+        # count from the device properties, the clock from the sampler (the
+        # maximum nvidia-smi reports while the timed steps ran)
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        sm_max = clocks.get("sm_max_mhz") or query_max_sm_mhz(local)
+        clk = n_sm * sm_max * 1e6
         if args.mode == "fp64":
             ops, lanes, pipe = fold, FP64_LANES, "FP64 pipe"
         else:
@@ -480,7 +629,11 @@ def main():
                 "traffic": profiled_traffic(args.mode, args.workload, batch.n_curves),
                 "kernel": "k_main", "kernel_ms": kern_ms, "kernel_point_trials_per_s": rate,
                 "pipe": pipe,
-                "peak_basis": f"{SM_COUNT} SMs x {lanes} lanes/clk x {SM_MAX_MHZ:.0f} MHz",
+                "peak_basis": f"{n_sm} SMs x {lanes} lanes/clk x {sm_max:.0f} MHz",
+                "sm_count": n_sm, "sm_max_mhz": sm_max,
+                "sm_count_from": "torch.cuda.get_device_properties().multi_processor_count",
+                "sm_max_mhz_from": "nvidia-smi clocks.max.sm, sampled during the timed steps"
+                if clocks.get("sm_max_mhz") else "nvidia-smi clocks.max.sm, queried once",
                 "ops_per_point_trial": ops}
         if args.mode == "split32":
             roof["fp32_pipe_frac"] = fold * rate / (FP32_LANES * clk)
@@ -509,6 +662,7 @@ def main():
             "clocks": clocks,
             "roofline": roof,
             "cpu_baseline": cpu,
+            "parity": parity,
             "modes": extras,
             "wall_s": wall,
         }

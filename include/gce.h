@@ -14,7 +14,9 @@
  *   - Array arguments are DEVICE pointers (cudaMalloc'd or managed) unless their
  *     name starts with h_, which marks HOST memory.  The caller owns every input
  *     and output buffer; the library never frees or keeps them past the call's
- *     stream work.
+ *     stream work.  Device arrays must live on the handle's device: an array
+ *     that the CUDA runtime reports as another device's memory is rejected with
+ *     GCE_ERR_INVALID before anything is launched.
  *   - A ragged batch is (times, mags, h_offsets, n_curves): curve c owns elements
  *     [h_offsets[c], h_offsets[c+1]) of times and mags (float64); h_offsets is a
  *     HOST int64 array of n_curves + 1 entries starting at 0, non-decreasing.
@@ -220,16 +222,19 @@ gce_status gce_ce_topk_host(gce_handle h, const double *h_times, const double *h
  * no handle: all its device workspace is a 32 MiB array built into the library
  * (held on every GPU where the library is loaded, until the process exits).
  * Arguments are those of gce_ce_topk, with the same meaning and layout; the
- * caller still owns the input and output buffers.  The call is synchronous on
- * `stream` and folds the device-side input checks into its status.
+ * caller still owns the input and output buffers.  The call runs on the
+ * calling thread's current device, and every device array must be there
+ * (GCE_ERR_INVALID otherwise).  The call is synchronous on `stream` and folds
+ * the device-side input checks into its status.
  * Returns GCE_ERR_NOMEM, launching nothing, when the job needs more than the
  * 32 MiB (about 16 B per point + 32 B per trial + 8 B per (curve, 512-trial
  * tile, k) + 0.5 MiB); use gce_ce_topk for larger jobs.  Returns
  * GCE_ERR_UNSUPPORTED when the bin counts need more shared memory than one CTA
  * of its fixed launch shape (256 threads, 2 trials each) can have.
- * The first call on a device sets that device up (finds the array's device
- * address, fills a table in it, with a few synchronous CUDA calls): make it
- * before any stream capture.  Every call shares the array and keeps the last
+ * Every call looks up the array's device address; the first call on a device
+ * (and the first after a device reset, which moves the array) also fills a
+ * table in it with a few synchronous CUDA calls: make the first call before
+ * any stream capture.  Every call shares the array and keeps the last
  * call's contents; each call rewrites what it reads.  Calls that overlap on the
  * GPU (two host threads or two streams) race on the array: make them one at a
  * time. */

@@ -181,18 +181,39 @@ def gce_check_job(offsets, n_periods, n_pdots, cfg: Config, k=0):
                                ctypes.byref(c), int(k))
 
 
-def _common(times, mags, offsets, periods, pdots):
+def one_device(named, device=None):
+    """The CUDA device index shared by every tensor of (name, tensor) pairs
+    (None entries skipped); raises ValueError if they lie on different devices or
+    not on `device` (a handle's device) when that is given."""
+    idx = None
+    for name, t in named:
+        if t is None:
+            continue
+        d = t.device.index
+        if idx is None:
+            idx = d
+        elif d != idx:
+            raise ValueError(f"{name} is on cuda:{d}, the other arrays on cuda:{idx}")
+    if device is not None and idx is not None and idx != device:
+        raise ValueError(f"the arrays are on cuda:{idx}, the handle on cuda:{device}")
+    return idx
+
+
+def _common(times, mags, offsets, periods, pdots, handle=None):
     import torch
     off, poff = _host_offsets(offsets)
-    return (off, poff, _dev(times, torch.float64, "times"), _dev(mags, torch.float64, "mags"),
-            _dev(periods, torch.float64, "periods"), _dev(pdots, torch.float64, "pdots"))
+    out = (off, poff, _dev(times, torch.float64, "times"), _dev(mags, torch.float64, "mags"),
+           _dev(periods, torch.float64, "periods"), _dev(pdots, torch.float64, "pdots"))
+    one_device([("times", times), ("mags", mags), ("periods", periods), ("pdots", pdots)],
+               None if handle is None else handle.device)
+    return out
 
 
 def gce_ce_grid(handle: Handle, times, mags, offsets, periods, pdots, cfg: Config, out=None,
                 stream=None):
     """H[n_curves, n_pdots, n_periods] (float32 CUDA tensor)."""
     import torch
-    off, poff, pt, pm, pp, pd = _common(times, mags, offsets, periods, pdots)
+    off, poff, pt, pm, pp, pd = _common(times, mags, offsets, periods, pdots, handle)
     nc = off.shape[0] - 1
     if out is None:
         out = torch.empty((nc, pdots.numel(), periods.numel()), dtype=torch.float32,
@@ -207,7 +228,7 @@ def gce_ce_grid(handle: Handle, times, mags, offsets, periods, pdots, cfg: Confi
 def gce_ce_grid_single(handle: Handle, times, mags, offsets, periods, pdots, cfg: Config,
                        out=None, stream=None):
     import torch
-    off, poff, pt, pm, pp, pd = _common(times, mags, offsets, periods, pdots)
+    off, poff, pt, pm, pp, pd = _common(times, mags, offsets, periods, pdots, handle)
     nc = off.shape[0] - 1
     if out is None:
         out = torch.empty((nc, pdots.numel(), periods.numel()), dtype=torch.float32,
@@ -224,7 +245,7 @@ def gce_ce_topk(handle: Handle, times, mags, offsets, periods, pdots, cfg: Confi
                 out_H=None, out_idx=None, stream=None):
     """(topk_H float32[n_curves, k], topk_idx int64[n_curves, k]) CUDA tensors."""
     import torch
-    off, poff, pt, pm, pp, pd = _common(times, mags, offsets, periods, pdots)
+    off, poff, pt, pm, pp, pd = _common(times, mags, offsets, periods, pdots, handle)
     nc = off.shape[0] - 1
     if out_H is None:
         out_H = torch.empty((nc, k), dtype=torch.float32, device=times.device)
@@ -244,7 +265,7 @@ def gce_ce_detect(handle: Handle, times, mags, offsets, periods, pdots, cfg: Con
     """(topk_H, topk_idx, mean, std, rho) CUDA tensors: the k smallest cells and the
     significance rho = (mean - H_min) / std of each curve (Eq. 5)."""
     import torch
-    off, poff, pt, pm, pp, pd = _common(times, mags, offsets, periods, pdots)
+    off, poff, pt, pm, pp, pd = _common(times, mags, offsets, periods, pdots, handle)
     nc = off.shape[0] - 1
     dev = times.device
     tH = torch.empty((nc, k), dtype=torch.float32, device=dev)
@@ -266,7 +287,7 @@ def gce_ce_grid_bands(handle: Handle, times, mags, bands, n_bands: int, offsets,
     """gce_ce_grid on multi-filter input: bands is a uint8 CUDA tensor (the filter
     of each point, < n_bands); each (curve, filter) is median/std normalised."""
     import torch
-    off, poff, pt, pm, pp, pd = _common(times, mags, offsets, periods, pdots)
+    off, poff, pt, pm, pp, pd = _common(times, mags, offsets, periods, pdots, handle)
     nc = off.shape[0] - 1
     if out is None:
         out = torch.empty((nc, pdots.numel(), periods.numel()), dtype=torch.float32,
@@ -284,7 +305,7 @@ def gce_ce_detect_bands(handle: Handle, times, mags, bands, n_bands: int, offset
     """gce_ce_detect on multi-filter input; (topk_H, topk_idx, mean, std, rho), the
     last three None when significance is False."""
     import torch
-    off, poff, pt, pm, pp, pd = _common(times, mags, offsets, periods, pdots)
+    off, poff, pt, pm, pp, pd = _common(times, mags, offsets, periods, pdots, handle)
     nc = off.shape[0] - 1
     dev = times.device
     tH = torch.empty((nc, k), dtype=torch.float32, device=dev)
@@ -354,10 +375,14 @@ def gce_ce_topk_static(times, mags, offsets, periods, pdots, cfg: Config, k: int
         out_H = torch.empty((nc, k), dtype=torch.float32, device=times.device)
     if out_idx is None:
         out_idx = torch.empty((nc, k), dtype=torch.int64, device=times.device)
+    one_device([("times", times), ("topk_H", out_H), ("topk_idx", out_idx)])
     c = cfg.c()
-    st = lib().gce_ce_topk_static(pt, pm, poff, nc, pp, periods.numel(), pd, pdots.numel(),
-                                  ctypes.byref(c), int(k), _dev(out_H, torch.float32, "topk_H"),
-                                  _dev(out_idx, torch.int64, "topk_idx"), _stream(stream))
+    # the call runs on the current device: make it the arrays' device
+    with torch.cuda.device(times.device):
+        st = lib().gce_ce_topk_static(pt, pm, poff, nc, pp, periods.numel(), pd, pdots.numel(),
+                                      ctypes.byref(c), int(k),
+                                      _dev(out_H, torch.float32, "topk_H"),
+                                      _dev(out_idx, torch.int64, "topk_idx"), _stream(stream))
     if st != GCE_OK:
         raise GceError(st, lib().gce_status_string(st).decode())
     return out_H, out_idx
@@ -367,7 +392,7 @@ def gce_ce_counts(handle: Handle, times, mags, offsets, periods, pdots, cfg: Con
                   cell_trial, stream=None):
     """uint32 counts[n_cells, n_mag_bins, n_phase_bins] as an int32 CUDA tensor view."""
     import torch
-    off, poff, pt, pm, pp, pd = _common(times, mags, offsets, periods, pdots)
+    off, poff, pt, pm, pp, pd = _common(times, mags, offsets, periods, pdots, handle)
     nc = off.shape[0] - 1
     n_cells = cell_curve.numel()
     counts = torch.empty((n_cells, cfg.n_mag_bins, cfg.n_phase_bins), dtype=torch.int32,
@@ -409,7 +434,7 @@ def gce_autotune(handle: Handle, cfg: Config, n_obs_hint: int, n_trials_hint: in
 
 def gce_autotune_job(handle: Handle, times, mags, offsets, periods, pdots, cfg: Config):
     """Tune the launch shape on a bounded slice of this job (see gce.h)."""
-    off, poff, pt, pm, pp, pd = _common(times, mags, offsets, periods, pdots)
+    off, poff, pt, pm, pp, pd = _common(times, mags, offsets, periods, pdots, handle)
     c = cfg.c()
     _check(lib().gce_autotune_job(handle.ptr, pt, pm, poff, off.shape[0] - 1, pp, periods.numel(),
                                   pd, pdots.numel(), ctypes.byref(c)), handle.ptr)

@@ -12,12 +12,13 @@
 // g_scratch is a file-scope __device__ array of kScratchBytes (32 MiB), so
 // every GPU on which the library is loaded holds it until the process exits.
 // The host never touches g_scratch by name: in host code that name is only a
-// stand-in, not a device address.  Once per device, with that device current,
-// setup() asks the runtime for the array's device address
-// (cudaGetSymbolAddress) and fills the c ln c table it holds; every call then
-// passes that address to the kernels.  The first call on a device does this
-// set-up (a few small synchronous CUDA calls), so it should be made before any
-// stream capture.
+// stand-in, not a device address.  Every call, with the caller's device current,
+// asks the runtime for the array's device address (cudaGetSymbolAddress, a
+// cheap lookup); the first call on a device, and any call that finds the
+// address moved (after a device reset the module is loaded anew), fills the
+// c ln c table held at the array's start (a few small synchronous CUDA calls),
+// so the first call on a device should be made before any stream capture.
+// Every call then passes that address to the kernels.
 //
 // Every call uses the same array, which keeps the previous call's contents.
 // Each call rewrites all of it that it reads (the job state is cleared by
@@ -25,6 +26,10 @@
 // they are read), so nothing depends on earlier contents.  Calls that overlap
 // on the GPU (from two host threads, or two streams) race on the array: issue
 // them one at a time.
+//
+// The call runs on the current device.  Every device array it is given must
+// live on that device (checked with cudaPointerGetAttributes; memory of another
+// device is GCE_ERR_INVALID).
 #include <cstdint>
 #include <cstring>
 #include <mutex>
@@ -45,6 +50,7 @@ struct DeviceSetup {
     bool done = false;
     unsigned char *base = nullptr;  // device address of g_scratch
     int n_sm = 0;
+    int smem_optin = 0;
 };
 
 std::mutex g_mutex;
@@ -93,11 +99,16 @@ gce_status setup(int dev, DeviceSetup *&out) {
     std::lock_guard<std::mutex> lock(g_mutex);
     if (dev < 0 || dev >= kMaxDevices) return fail(GCE_ERR_UNSUPPORTED, "device index too large");
     DeviceSetup &d = g_setup[dev];
-    if (!d.done) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess) return fail(GCE_ERR_CUDA, cudaGetErrorString(e));
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess) return fail(GCE_ERR_CUDA, cudaGetErrorString(e));
+    if (!d.done || d.base != static_cast<unsigned char *>(p)) {
+        // first use on this device, or the module was loaded anew (the array moved
+        // and its table is gone): fill the c ln c table again
+        d.done = false;
         e = cudaDeviceGetAttribute(&d.n_sm, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return fail(GCE_ERR_CUDA, cudaGetErrorString(e));
+        e = cudaDeviceGetAttribute(&d.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         if (e != cudaSuccess) return fail(GCE_ERR_CUDA, cudaGetErrorString(e));
         e = launch_table(reinterpret_cast<unsigned long long *>(p), (int)kTableEntries - 1, 0);
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -107,6 +118,18 @@ gce_status setup(int dev, DeviceSetup *&out) {
     }
     out = &d;
     return GCE_OK;
+}
+
+// A device array of the call must be on the current device: memory that the
+// runtime reports as another device's is rejected (managed and host-registered
+// memory is left to the driver).
+bool on_device(const void *ptr, int dev) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return true;  // not a pointer the runtime knows: left to the kernels' own access
+    }
+    return a.type != cudaMemoryTypeDevice || a.device == dev;
 }
 
 }  // namespace
@@ -128,6 +151,9 @@ extern "C" gce_status gce_ce_topk_static(const double *times, const double *mags
     if (e != cudaSuccess) return fail(GCE_ERR_CUDA, cudaGetErrorString(e));
     DeviceSetup *d = nullptr;
     if ((st = setup(dev, d)) != GCE_OK) return st;
+    const void *arrays[] = {times, mags, periods, pdots, topk_H, topk_idx};
+    for (const void *a : arrays)
+        if (!on_device(a, dev)) return fail(GCE_ERR_INVALID, "an array is on another device");
     cudaStream_t s = (cudaStream_t)stream;
     const int mode = cfg->phase_mode;
 
@@ -144,10 +170,8 @@ extern "C" gce_status gce_ce_topk_static(const double *times, const double *mags
     const int narrow = (mode == GCE_PHASE_SPLIT32 && n_pdots > 1) ? 1 : 0;
     const size_t smem = main_smem_bytes(mode, block, tpt, chunk, cfg->n_phase_bins,
                                         cfg->n_mag_bins, table_smem, k, narrow);
-    int optin = 0;
-    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (e != cudaSuccess) return fail(GCE_ERR_CUDA, cudaGetErrorString(e));
-    if (smem > (size_t)optin) return fail(GCE_ERR_UNSUPPORTED, "bin counts too large for this entry point");
+    if (smem > main_dynamic_smem_limit(mode, tpt, block, (size_t)d->smem_optin))
+        return fail(GCE_ERR_UNSUPPORTED, "bin counts too large for this entry point");
     const TileGrid tg = tile_grid(n_periods, n_pdots, block, tpt);
     const long long n_tiles = tg.n_tiles;
     const int point_bytes = mode == GCE_PHASE_FP64 ? 8 : 16;
@@ -155,7 +179,7 @@ extern "C" gce_status gce_ce_topk_static(const double *times, const double *mags
     if (L.end > kScratchBytes)
         return fail(GCE_ERR_NOMEM, "job needs more than the 32 MiB of built-in scratch");
 
-    e = main_kernel_attrs(mode, tpt, block, smem);
+    e = main_kernel_attrs(mode, tpt, block, (size_t)d->smem_optin);
     if (e != cudaSuccess) return fail(GCE_ERR_CUDA, cudaGetErrorString(e));
     int occ = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, main_kernel_ptr(mode, tpt, block), block, smem);

@@ -97,3 +97,24 @@ def test_loading_fails_loudly_without_the_library(monkeypatch):
     monkeypatch.setattr(binding, "_lib", None)
     with pytest.raises(RuntimeError, match="missing"):
         binding.lib()
+
+
+def test_binding_rejects_arrays_on_different_devices():
+    """The binding's device check (no GPU needed: stand-ins carry only a device):
+    every array of a call must share one CUDA device, and that device must be the
+    handle's when a handle is given."""
+    from types import SimpleNamespace as NS
+
+    import torch
+
+    from paper_2006_06866_gb300.binding import one_device
+
+    def on(i):
+        return NS(device=torch.device("cuda", i))
+
+    assert one_device([("times", on(1)), ("mags", on(1)), ("out", None)]) == 1
+    assert one_device([("times", on(0)), ("mags", on(0))], device=0) == 0
+    with pytest.raises(ValueError, match="mags is on cuda:1"):
+        one_device([("times", on(0)), ("mags", on(1))])
+    with pytest.raises(ValueError, match="handle on cuda:0"):
+        one_device([("times", on(1)), ("mags", on(1))], device=0)

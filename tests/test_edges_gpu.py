@@ -231,6 +231,32 @@ def test_graph_replay_with_new_inputs(h, use_graph):
             assert np.abs(got - ref).max() <= 1e-6
 
 
+def test_graph_replay_sees_new_contents_in_place(h):
+    """Same shape and the same device arrays, new contents written in place
+    (including a new t0 and new curve lengths at the same total): the cached graph
+    is replayed without a new capture and computes on the new contents."""
+    orc = oracle.Oracle()
+    s = torch.cuda.Stream()
+    b0 = small_batch(seed=21, pdots=(0.0, -1e-11))
+    args = dev_args(b0)
+    out = torch.empty((b0.n_curves, b0.pdots.size, b0.periods.size), dtype=torch.float32,
+                      device="cuda")
+    with torch.cuda.stream(s):
+        for seed, t0 in ((21, 0.0), (22, 0.0), (23, 0.0), (24, 0.0), (25, 3.0e7)):
+            b = small_batch(seed=seed, pdots=(0.0, -1e-11))
+            offs = b.offsets.copy()
+            if seed == 24:  # other lengths, same total number of points
+                offs[1:-1] += np.array([50, -30])
+            args["times"].copy_(torch.tensor(b.times))
+            args["mags"].copy_(torch.tensor(b.mags))
+            args["offsets"] = offs
+            cfg = g.Config(15, 10, "fp64", t0=t0)
+            g.gce_ce_grid(h, cfg=cfg, out=out, stream=s, **args)
+            assert g.gce_stream_status(h, s) == g.GCE_OK
+            ref = orc.ce_grid(b.times, b.mags, offs, b.periods, b.pdots, 15, 10, t0=t0)
+            assert np.abs(out.cpu().numpy() - ref).max() <= 1e-6, seed
+
+
 @pytest.mark.parametrize("mode", ["fp64", "fixed32"])
 def test_host_entry_point_matches_device(h, mode):
     b = small_batch(seed=8, n_curves=4, pdots=(0.0, -2e-11))
