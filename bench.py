@@ -457,6 +457,7 @@ def main():
 
     tuned = {}
     launches = {}
+    host_ms = {}  # mean host time of one step's call (argument checks, planning, enqueue)
 
     def timed_steps(mode, warmup, steps, with_kernel=False):
         if mode not in tuned:  # launch-shape autotuning is part of the untimed warm-up
@@ -474,13 +475,16 @@ def main():
             evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                    for _ in range(steps)]
             kern = []
+            host = []
             barrier()
             torch.cuda.synchronize()
             wall0 = time.perf_counter()
             for i in range(steps):
                 flush.zero_()
                 evs[i][0].record(stream)
+                h0 = time.perf_counter()
                 step(mode, time_kernel=with_kernel)
+                host.append(time.perf_counter() - h0)
                 evs[i][1].record(stream)
                 if with_kernel:
                     kern.append(g.gce_kernel_time(h))
@@ -493,6 +497,7 @@ def main():
         if st != g.GCE_OK:
             raise RuntimeError(f"device input check failed: status {st}")
         ms = sum(a.elapsed_time(b) for a, b in evs)
+        host_ms[mode] = 1e3 * float(np.mean(host))
         return ms, wall, kern
 
     # ---- headline: the batched persistent kernel in the headline fold mode
@@ -659,6 +664,7 @@ def main():
             "e2e": {"value": pt_step * args.steps * world / e2e_t, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches[args.mode],
+            "host_call_ms": host_ms.get(args.mode),
             "clocks": clocks,
             "roofline": roof,
             "cpu_baseline": cpu,

@@ -44,6 +44,37 @@ struct GraphKey {
     }
 };
 
+// Everything a captured call sequence bakes into its nodes besides the launch
+// shape (which the GraphKey holds): the caller's arrays, the epoch, the flags,
+// and the handle's own workspace and pinned staging buffers.  A call whose
+// fingerprint equals the cached graph's replays that graph as it is.
+struct Fingerprint {
+    uintptr_t v[40];
+    int n = 0;
+    void add(const void *p) { v[n++] = (uintptr_t)p; }
+    void add_u(unsigned long long x) { v[n++] = (uintptr_t)x; }
+    bool operator==(const Fingerprint &o) const {
+        return n == o.n && std::memcmp(v, o.v, sizeof(uintptr_t) * (size_t)n) == 0;
+    }
+};
+
+// The inputs of a launch shape's fitting (mode, bins, longest curve, top-k,
+// slot range, the tuning's block / tpt / chunk / CTA cap) and its result, so
+// that repeated calls skip the driver queries of the fitting.
+typedef std::tuple<int, int, int, int, int, int, int, int, int, int> ShapeKey;
+struct LaunchShape {
+    int block, tpt, chunk, table_smem, occ;
+    size_t smem;
+};
+
+constexpr int kCheckedArrays = 14;
+
+struct CachedGraph {
+    cudaGraphExec_t exec = nullptr;
+    Fingerprint fp;
+    int launches = 0;  // kernels the sequence launches
+};
+
 }  // namespace
 
 struct gce_handle_s {
@@ -64,7 +95,9 @@ struct gce_handle_s {
     bool timed = false;
     int launches = 0;                    // kernels the last job launched (directly or in its graph)
     std::map<TuneKey, gce_tuning> tune;
-    std::map<GraphKey, cudaGraphExec_t> graphs;
+    std::map<GraphKey, CachedGraph> graphs;
+    std::map<ShapeKey, LaunchShape> shapes;  // launch shapes already fitted to the device
+    const void *checked[kCheckedArrays] = {};  // arrays of the last call found on the device
 };
 
 static std::string g_create_error;
@@ -235,7 +268,7 @@ extern "C" gce_status gce_destroy(gce_handle h) {
     if (!h) return GCE_ERR_INVALID;
     cudaSetDevice(h->device);
     cudaDeviceSynchronize();
-    for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
+    for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second.exec);
     DevBuf *bufs[] = {&h->payload, &h->seg, &h->trialc, &h->order, &h->offsets, &h->cand, &h->stats,
                       &h->table, &h->state, &h->in_times, &h->in_mags, &h->in_periods,
                       &h->in_pdots, &h->out_H, &h->out_idx, &h->band_stats, &h->cand2,
@@ -275,11 +308,15 @@ struct Job {
 };
 
 struct Plan {
-    long long n_points, n_trials, n_items;
+    long long n_points, n_trials, n_items, n_long_items;
+    int n_long, n_short;  // curves taken curve-major / tile-major (see MainArgs)
     int n_max, n_tiles, n_ptiles, pd_major, narrow, block, tpt, grid, chunk, table_smem, grab;
     int n_groups, tiles_per_group;  // top-k: first merge level (0 groups: none)
     size_t smem;
 };
+
+// Curves of at most this many points are scheduled tile-major (Plan).
+constexpr long long kShortCurve = 256;
 
 gce_status make_plan(gce_handle h, const Job &j, Plan &pl) {
     const gce_config *cfg = j.cfg;
@@ -289,70 +326,94 @@ gce_status make_plan(gce_handle h, const Job &j, Plan &pl) {
     for (int c = 0; c < j.n_curves; ++c) nmax = std::max<long long>(nmax, j.h_offsets[c + 1] - j.h_offsets[c]);
     pl.n_max = (int)nmax;
     const gce_tuning t = j.force ? *j.force : lookup_tuning(h, cfg, pl.n_max, j.n_pdots > 1 ? 1 : 0);
-    pl.block = t.block;
-    pl.tpt = t.tpt;
-    pl.chunk = std::min(t.chunk, ((pl.n_max + 31) / 32) * 32);
-    // the c ln c table in shared memory: the whole table when it has at most
-    // 2048 entries (16 KB), so that lookups need no bounds test; longer curves
-    // read counts above it from global memory
-    pl.table_smem = std::min(pl.n_max + 1, 2048);
     const int kk = j.kind == JOB_TOPK ? j.k : 0;
     // a Pdot axis: SPLIT32 keeps the narrow slot range (every fold re-reduced)
     pl.narrow = (cfg->phase_mode == GCE_PHASE_SPLIT32 && j.n_pdots > 1) ? 1 : 0;
-    // shrink the staged chunk, then the table, then trials per thread, then the
-    // block, until the CTA fits in shared memory
-    auto size = [&]() {
-        return main_smem_bytes(cfg->phase_mode, pl.block, pl.tpt, pl.chunk, cfg->n_phase_bins,
-                               cfg->n_mag_bins, pl.table_smem, kk, pl.narrow);
-    };
-    pl.smem = size();
-    while (pl.smem > (size_t)h->smem_optin) {
-        if (pl.chunk > 512) pl.chunk /= 2;
-        else if (pl.table_smem > 256) pl.table_smem /= 2;
-        else if (pl.tpt > 1) pl.tpt /= 2;
-        else if (pl.block > 64) pl.block /= 2;
-        else if (pl.chunk > 64) pl.chunk /= 2;
-        else break;
+    const ShapeKey skey(cfg->phase_mode, cfg->n_phase_bins, cfg->n_mag_bins, pl.n_max, kk,
+                        pl.narrow, t.block, t.tpt, t.chunk, t.ctas_per_sm);
+    int occ = 0;
+    auto sit = h->shapes.find(skey);
+    if (sit != h->shapes.end()) {
+        const LaunchShape &ls = sit->second;
+        pl.block = ls.block;
+        pl.tpt = ls.tpt;
+        pl.chunk = ls.chunk;
+        pl.table_smem = ls.table_smem;
+        pl.smem = ls.smem;
+        occ = ls.occ;
+    } else {
+        pl.block = t.block;
+        pl.tpt = t.tpt;
+        pl.chunk = std::min(t.chunk, ((pl.n_max + 31) / 32) * 32);
+        // the c ln c table in shared memory: the whole table when it has at most
+        // 2048 entries (16 KB), so that lookups need no bounds test; longer curves
+        // read counts above it from global memory
+        pl.table_smem = std::min(pl.n_max + 1, 2048);
+        // shrink the staged chunk, then the table, then trials per thread, then the
+        // block, until the CTA fits in shared memory
+        auto size = [&]() {
+            return main_smem_bytes(cfg->phase_mode, pl.block, pl.tpt, pl.chunk, cfg->n_phase_bins,
+                                   cfg->n_mag_bins, pl.table_smem, kk, pl.narrow);
+        };
+        auto limit = [&]() {
+            return main_dynamic_smem_limit(cfg->phase_mode, pl.tpt, pl.block, (size_t)h->smem_optin);
+        };
         pl.smem = size();
+        while (pl.smem > limit()) {
+            if (pl.chunk > 512) pl.chunk /= 2;
+            else if (pl.table_smem > 256) pl.table_smem /= 2;
+            else if (pl.tpt > 1) pl.tpt /= 2;
+            else if (pl.block > 64) pl.block /= 2;
+            else if (pl.chunk > 64) pl.chunk /= 2;
+            else break;
+            pl.smem = size();
+        }
+        if (pl.smem > limit())
+            return fail(h, GCE_ERR_UNSUPPORTED, "launch shape needs %zu bytes of shared memory", pl.smem);
+        CUDA_TRY(h, main_kernel_attrs(cfg->phase_mode, pl.tpt, pl.block, (size_t)h->smem_optin));
+        const void *kern = main_kernel_ptr(cfg->phase_mode, pl.tpt, pl.block);
+        CUDA_TRY(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, pl.block, pl.smem));
+        if (occ < 1) return fail(h, GCE_ERR_UNSUPPORTED, "launch shape does not fit on an SM");
+        // A smaller staged chunk costs only more staging passes: take it whenever it
+        // admits more CTAs per SM (the counters leave little room at many phase bins,
+        // and the top-k buffer grows with k, so the tuned chunk can sit just past an
+        // occupancy step for another k).
+        // Every halving down to 256 points is tried; the largest chunk that reaches
+        // the best occupancy is kept.
+        {
+            int best_chunk = pl.chunk;
+            size_t best_smem = pl.smem;
+            for (int c = pl.chunk; c > 256;) {
+                c = std::max(256, (c / 2 + 31) / 32 * 32);
+                pl.chunk = c;
+                const size_t sm2 = size();
+                int occ2 = 0;
+                CUDA_TRY(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, kern, pl.block, sm2));
+                if (occ2 > occ) {
+                    occ = occ2;
+                    best_chunk = c;
+                    best_smem = sm2;
+                }
+            }
+            pl.chunk = best_chunk;
+            pl.smem = best_smem;
+        }
+        h->shapes[skey] = LaunchShape{pl.block, pl.tpt, pl.chunk, pl.table_smem, occ, pl.smem};
     }
-    if (pl.smem > (size_t)h->smem_optin)
-        return fail(h, GCE_ERR_UNSUPPORTED, "launch shape needs %zu bytes of shared memory", pl.smem);
     const TileGrid tg = tile_grid(j.n_periods, j.n_pdots, pl.block, pl.tpt);
     pl.n_tiles = (int)tg.n_tiles;
     pl.n_ptiles = tg.n_ptiles;
     pl.pd_major = tg.pd_major;
     pl.n_items = (long long)j.n_curves * pl.n_tiles;
+    // curves of at most kShortCurve points run tile-major: a CTA then takes one
+    // tile for several curves and loads its trial constants once
+    pl.n_short = 0;
+    for (int c = 0; c < j.n_curves; ++c)
+        if (j.h_offsets[c + 1] - j.h_offsets[c] <= kShortCurve) ++pl.n_short;
+    pl.n_long = j.n_curves - pl.n_short;
+    pl.n_long_items = (long long)pl.n_long * pl.n_tiles;
     pl.n_groups = j.kind == JOB_TOPK ? topk_groups(pl.n_tiles, j.k, &pl.tiles_per_group) : 0;
     if (j.kind != JOB_TOPK) pl.tiles_per_group = 0;
-    CUDA_TRY(h, main_kernel_attrs(cfg->phase_mode, pl.tpt, pl.block, pl.smem));
-    const void *kern = main_kernel_ptr(cfg->phase_mode, pl.tpt, pl.block);
-    int occ = 0;
-    CUDA_TRY(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, pl.block, pl.smem));
-    if (occ < 1) return fail(h, GCE_ERR_UNSUPPORTED, "launch shape does not fit on an SM");
-    // A smaller staged chunk costs only more staging passes: take it whenever it
-    // admits more CTAs per SM (the counters leave little room at many phase bins,
-    // and the top-k buffer grows with k, so the tuned chunk can sit just past an
-    // occupancy step for another k).
-    // Every halving down to 256 points is tried; the largest chunk that reaches
-    // the best occupancy is kept.
-    {
-        int best_chunk = pl.chunk;
-        size_t best_smem = pl.smem;
-        for (int c = pl.chunk; c > 256;) {
-            c = std::max(256, (c / 2 + 31) / 32 * 32);
-            pl.chunk = c;
-            const size_t sm2 = size();
-            int occ2 = 0;
-            CUDA_TRY(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, kern, pl.block, sm2));
-            if (occ2 > occ) {
-                occ = occ2;
-                best_chunk = c;
-                best_smem = sm2;
-            }
-        }
-        pl.chunk = best_chunk;
-        pl.smem = best_smem;
-    }
     if (t.ctas_per_sm > 0) occ = std::min(occ, t.ctas_per_sm);
     long long g = (long long)h->n_sm * occ;
     g = std::min(g, std::max(pl.n_items, 1ll));
@@ -429,6 +490,9 @@ gce_status enqueue(gce_handle h, const Job &j, const Plan &pl, cudaStream_t s, b
     ma.pd_major = pl.pd_major;
     ma.narrow = pl.narrow;
     ma.n_items = pl.n_items;
+    ma.n_long_items = pl.n_long_items;
+    ma.n_long = pl.n_long;
+    ma.n_short = pl.n_short;
     ma.grab = pl.grab;
     ma.n_phase = cfg->n_phase_bins;
     ma.n_mag = cfg->n_mag_bins;
@@ -496,6 +560,18 @@ gce_status enqueue(gce_handle h, const Job &j, const Plan &pl, cudaStream_t s, b
     return GCE_OK;
 }
 
+// A device array must be on the handle's device: memory the runtime reports as
+// another device's is rejected (managed and host-registered memory is left to
+// the driver).
+bool on_device(const void *ptr, int dev) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return a.type != cudaMemoryTypeDevice || a.device == dev;
+}
+
 gce_status run_job(gce_handle h, const Job &j, cudaStream_t s) {
     if (!h) return GCE_ERR_INVALID;
     h->launches = 0;
@@ -519,6 +595,20 @@ gce_status run_job(gce_handle h, const Job &j, cudaStream_t s) {
     if (j.bands && (j.n_bands < 1 || j.n_bands > GCE_MAX_BANDS))
         return fail(h, GCE_ERR_INVALID, "n_bands must be 1 .. %d", GCE_MAX_BANDS);
     CUDA_TRY(h, cudaSetDevice(h->device));
+    {
+        // arrays already checked by the previous call (same argument, same
+        // pointer) need no new query
+        const void *arrays[kCheckedArrays] = {j.times, j.mags, j.periods, j.pdots, j.out,
+                                              j.topk_H, j.topk_idx, j.mean, j.std_dev, j.rho,
+                                              j.cell_curve, j.cell_trial, j.counts, j.bands};
+        for (int i = 0; i < kCheckedArrays; ++i) {
+            if (arrays[i] && arrays[i] != h->checked[i] && !on_device(arrays[i], h->device)) {
+                std::fill(h->checked, h->checked + kCheckedArrays, nullptr);
+                return fail(h, GCE_ERR_INVALID, "an array is on another device than the handle's");
+            }
+            h->checked[i] = arrays[i];
+        }
+    }
 
     Plan pl;
     gce_status st = make_plan(h, j, pl);
@@ -582,47 +672,71 @@ gce_status run_job(gce_handle h, const Job &j, cudaStream_t s) {
         st = enqueue(h, j, pl, s, false);
         if (st != GCE_OK) return st;
     } else {
-        cudaGraph_t graph = nullptr;
-        CUDA_TRY(h, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-        st = enqueue(h, j, pl, s, true);
-        cudaError_t e = cudaStreamEndCapture(s, &graph);
-        if (st != GCE_OK) {
-            if (graph) cudaGraphDestroy(graph);
-            return st;
-        }
-        if (e != cudaSuccess) return fail(h, GCE_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
         GraphKey key{j.kind * 8 + (j.bands ? 4 : 0) + (j.rho ? 2 : 0) +
                          ((j.cfg->flags & GCE_FLAG_OVERLAP) ? 1 : 0),
                      mode, j.n_curves, j.n_periods, j.n_pdots, j.cfg->n_phase_bins,
                      j.cfg->n_mag_bins, j.k, pl.block, pl.tpt, pl.grid, pl.chunk, pl.table_smem,
                      pl.grab, pl.n_points};
+        Fingerprint fp;
+        const void *ptrs[] = {j.times, j.mags, j.periods, j.pdots, j.out, j.topk_H, j.topk_idx,
+                              j.mean, j.std_dev, j.rho, j.cell_curve, j.cell_trial, j.counts,
+                              j.bands, h->payload.p, h->seg.p, h->trialc.p, h->order.p,
+                              h->offsets.p, h->cand.p, h->stats.p, h->cand2.p, h->stats2.p,
+                              h->table.p, h->state.p, h->band_stats.p, h->h_order, h->h_offsets};
+        for (const void *p : ptrs) fp.add(p);
+        unsigned long long t0_bits;
+        std::memcpy(&t0_bits, &j.cfg->t0, sizeof(t0_bits));
+        fp.add_u(t0_bits);
+        fp.add_u(j.cfg->flags);
+        fp.add_u((unsigned long long)j.n_bands);
+        fp.add_u((unsigned long long)j.n_cells);
+        fp.add_u((unsigned long long)pl.n_long);
         auto it = h->graphs.find(key);
-        bool ready = false;
-        if (it != h->graphs.end()) {
-            cudaGraphExecUpdateResultInfo info;
-            if (cudaGraphExecUpdate(it->second, graph, &info) == cudaSuccess) {
-                ready = true;
-            } else {
-                cudaGetLastError();
-                cudaGraphExecDestroy(it->second);
-                h->graphs.erase(it);
+        if (it != h->graphs.end() && it->second.fp == fp) {
+            // same shape and the same arrays as the cached graph: replay it as it is
+            h->launches += it->second.launches;
+        } else {
+            const int before = h->launches;
+            cudaGraph_t graph = nullptr;
+            CUDA_TRY(h, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            st = enqueue(h, j, pl, s, true);
+            cudaError_t e = cudaStreamEndCapture(s, &graph);
+            if (st != GCE_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return st;
             }
+            if (e != cudaSuccess) return fail(h, GCE_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+            bool ready = false;
+            if (it != h->graphs.end()) {
+                // same shape, other arrays: update the cached graph's parameters
+                cudaGraphExecUpdateResultInfo info;
+                if (cudaGraphExecUpdate(it->second.exec, graph, &info) == cudaSuccess) {
+                    ready = true;
+                } else {
+                    cudaGetLastError();
+                    cudaGraphExecDestroy(it->second.exec);
+                    h->graphs.erase(it);
+                }
+            }
+            if (!ready) {
+                cudaGraphExec_t exec = nullptr;
+                e = cudaGraphInstantiate(&exec, graph, 0);
+                if (e != cudaSuccess) {
+                    cudaGraphDestroy(graph);
+                    return fail(h, GCE_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+                }
+                if (h->graphs.size() > 64) {
+                    for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second.exec);
+                    h->graphs.clear();
+                }
+                h->graphs[key].exec = exec;
+            }
+            cudaGraphDestroy(graph);
+            CachedGraph &cg = h->graphs[key];
+            cg.fp = fp;
+            cg.launches = h->launches - before;
         }
-        if (!ready) {
-            cudaGraphExec_t exec = nullptr;
-            e = cudaGraphInstantiate(&exec, graph, 0);
-            if (e != cudaSuccess) {
-                cudaGraphDestroy(graph);
-                return fail(h, GCE_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
-            }
-            if (h->graphs.size() > 64) {
-                for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
-                h->graphs.clear();
-            }
-            h->graphs[key] = exec;
-        }
-        cudaGraphDestroy(graph);
-        CUDA_TRY(h, cudaGraphLaunch(h->graphs[key], s));
+        CUDA_TRY(h, cudaGraphLaunch(h->graphs[key].exec, s));
     }
     CUDA_TRY(h, cudaEventRecord(h->staged, s));
     h->staged_pending = true;

@@ -376,6 +376,11 @@ struct MainArgs {
     int pd_major;              // tile = block periods x tpt Pdot values (else flat runs)
     int narrow;                // SPLIT32: narrow slot range, every fold re-reduced
     long long n_items;         // n_curves * n_tiles
+    // items [0, n_long_items) are (curve, tile) pairs of the first n_long curves
+    // of `order`, curve-major; the rest pair the n_short curves after them with
+    // the tiles tile-major (curve index fastest)
+    long long n_long_items;
+    int n_long, n_short;
     int grab;                  // items taken per work-counter increment
     int n_phase;
     int n_mag;
@@ -403,7 +408,8 @@ cudaError_t launch_table(unsigned long long *table, int n_max, cudaStream_t s);
 size_t main_smem_bytes(int mode, int block, int tpt, int chunk, int n_phase, int n_mag,
                        int table_smem, int k, int narrow);
 size_t single_smem_bytes(int n_phase, int block);
-cudaError_t main_kernel_attrs(int mode, int tpt, int block, size_t smem);
+size_t main_dynamic_smem_limit(int mode, int tpt, int block, size_t smem_optin);
+cudaError_t main_kernel_attrs(int mode, int tpt, int block, size_t smem_optin);
 const void *main_kernel_ptr(int mode, int tpt, int block);
 cudaError_t launch_main(int mode, int tpt, int block, int grid, size_t smem,
                         const MainArgs &a, cudaStream_t s);

@@ -44,29 +44,6 @@ __device__ __forceinline__ unsigned long long warp_min_key(unsigned long long v)
 }
 
 
-// c ln c from the fixed-point table: shared memory when every count of the curve
-// is covered there (ALL_SMEM), else shared below table_smem and global above.
-template <bool ALL_SMEM>
-__device__ __forceinline__ unsigned long long tab_lookup(const unsigned long long *s_tab,
-                                                         int table_smem,
-                                                         const unsigned long long *g_tab,
-                                                         int c) {
-    if (ALL_SMEM) return s_tab[c];
-    return c < table_smem ? s_tab[c] : __ldg(g_tab + c);
-}
-// The same from d = c << 16 (low 16 bits zero): the byte offset c * 8 is d >> 13.
-template <bool ALL_SMEM>
-__device__ __forceinline__ unsigned long long tab_lookup16(const unsigned long long *s_tab,
-                                                           int table_smem,
-                                                           const unsigned long long *g_tab,
-                                                           unsigned int d) {
-    if (ALL_SMEM)
-        return *reinterpret_cast<const unsigned long long *>(
-            reinterpret_cast<const char *>(s_tab) + (d >> 13));
-    return tab_lookup<false>(s_tab, table_smem, g_tab, (int)(d >> 16));
-}
-
-
 // Per-mode constants of the fold, computed once per kernel.
 struct FoldConst {
     double nphi_d;
@@ -185,8 +162,8 @@ template <> struct Fold<GCE_PHASE_FIXED32> {
 // The increment carries no memory clobber, so the compiler may schedule the
 // next points' shared loads around it; compiler_fence() before and after each
 // hot loop keeps the counters' plain loads and stores on their side of it.
-__device__ __forceinline__ void red_shared_inc(unsigned int addr) {
-    asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(addr));
+__device__ __forceinline__ void red_shared_add(unsigned int addr, unsigned int inc) {
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(inc));
 }
 __device__ __forceinline__ void compiler_fence() { asm volatile("" ::: "memory"); }
 
@@ -202,7 +179,7 @@ template <int MODE, int TPT, int SH, bool PDOT, bool K0, bool RED, bool SHARED>
 __device__ __forceinline__ void count_points(
     const typename ModeTraits<MODE>::point_t *__restrict__ pts, int ka, int kb,
     const typename Fold<MODE>::prep_t (&tc)[TPT], const unsigned int (&base)[TPT],
-    const FoldConst &fk) {
+    const FoldConst &fk, unsigned int inc) {
 #pragma unroll 8
     for (int k = ka; k < kb; ++k) {
         const typename ModeTraits<MODE>::point_t p = pts[k];
@@ -223,7 +200,7 @@ __device__ __forceinline__ void count_points(
                 continue;
             }
 #endif
-            red_shared_inc(addr);
+            red_shared_add(addr, inc);
         }
     }
 }
@@ -232,10 +209,10 @@ template <int MODE, int TPT, int SH, bool PDOT, bool K0, bool RED = false>
 __device__ __forceinline__ void count_points_any(
     bool shared, const typename ModeTraits<MODE>::point_t *__restrict__ pts, int ka, int kb,
     const typename Fold<MODE>::prep_t (&tc)[TPT], const unsigned int (&base)[TPT],
-    const FoldConst &fk) {
+    const FoldConst &fk, unsigned int inc) {
     constexpr bool SH_OK = PDOT && TPT > 1;  // sharing pays only with a Pdot term
-    if (SH_OK && shared) count_points<MODE, TPT, SH, PDOT, K0, RED, SH_OK>(pts, ka, kb, tc, base, fk);
-    else count_points<MODE, TPT, SH, PDOT, K0, RED, false>(pts, ka, kb, tc, base, fk);
+    if (SH_OK && shared) count_points<MODE, TPT, SH, PDOT, K0, RED, SH_OK>(pts, ka, kb, tc, base, fk, inc);
+    else count_points<MODE, TPT, SH, PDOT, K0, RED, false>(pts, ka, kb, tc, base, fk, inc);
 }
 
 // c_ij of one phase bin at the end of a magnitude segment (low - snapshot), with
@@ -248,101 +225,214 @@ __device__ __forceinline__ int take_segment(unsigned int *w) {
     return (int)((nv - v) >> 16);
 }
 
-// For each of the thread's TPT trials, sum_j T(c_j) over the phase bins, where
-// bin j's count is spread over the logical slots l in [L, R] with l = j (mod
-// n_phase): l, l + n_phase and, only in a window 2 n_phase wide or more,
-// l + 2 n_phase.  Trial s's slot l is the word wb[s] + (l + off) stride_j.
-// SEG: the counts since the last segment end, each slot's snapshot moved up to
-// its count (take_segment's update); else the cumulative counts.  Slot values
-// stay shifted left by 16 until the lookup, so a bin's slots add without a
-// shift.  OVL (50 %-overlapping bins, Sec. 2.3): overlapping bin j holds the
-// fine bins j and j + 1, so the sum is over T(c_j + c_{j+1}) of consecutive fine
-// bins (the bins are visited in cyclic order), closed by the last and the
-// first.  Each step loads the counters of a few bins of every trial before it
-// stores any, so the loads overlap instead of waiting on the previous stores.
-template <int TPT, bool SEG, bool ALL_SMEM, bool OVL>
-struct BinWindow {
-    unsigned int *const (&wb)[TPT];
-    const int off;  // physical slot of logical slot 0
-    const int stride_j;
-    const unsigned long long *s_tab;
-    const int table_smem;
-    const unsigned long long *g_tab;
-    // OVL: the first and the previous fine bin's count (shifted left by 16)
-    unsigned int first[TPT] = {}, prev[TPT] = {};
-    bool started = false;
+// Counter word formats.  Each (trial, slot) has one 32-bit shared word.
+//   FMT_SNAP: (snapshot << 16) | count, for curves of up to 65535 points.  The
+//     count is cumulative; the snapshot is the count at the end of the previous
+//     magnitude segment, so the segment's count is count - snapshot.
+//   FMT_PK2: (C << 20) | (B << 10) | A, for curves of at most kPk2MaxN points.
+//     Consecutive non-empty magnitude segments alternate between the fields A
+//     (increment 1) and B (increment 1 << 10); C is the cumulative count of the
+//     segments already swept.  One sweep then serves two segments: it reads A and
+//     B, adds them to C and clears them.  No field can overflow: each is at most
+//     the curve's point count.
+enum { FMT_SNAP = 0, FMT_PK2 = 1 };
+constexpr int kPk2MaxN = 1023;
+constexpr unsigned int kPk2IncB = 1u << 10;
 
-    // G bins starting at first slot l, each with C slots (l, l + n, l + 2n)
-    template <int G, int C>
-    __device__ __forceinline__ void step(int l, int n, unsigned long long (&acc)[TPT]) {
-        unsigned int *p[TPT][G][C];
-        unsigned int v[TPT][G][C];
+// Per counter word: the byte offsets 8 c into the c ln c table of the counts a
+// sweep reads, and the word it leaves behind.
+template <int FMT, bool SEG> struct Fields;
+template <> struct Fields<FMT_SNAP, true> {  // the segment's count; snapshot moved up
+    static constexpr int NF = 1;
+    __device__ __forceinline__ static unsigned int get(unsigned int v, unsigned int (&o)[1]) {
+        const unsigned int nv = __byte_perm(v, 0u, 0x1010);
+        o[0] = (nv - v) >> 13;
+        return nv;
+    }
+    // an extra slot's segment count joins its bin's first word
+    __device__ __forceinline__ static unsigned int merge(unsigned int first, unsigned int extra) {
+        return first + (extra & 0xffffu) - (extra >> 16);
+    }
+};
+template <> struct Fields<FMT_SNAP, false> {  // the cumulative count; word cleared
+    static constexpr int NF = 1;
+    __device__ __forceinline__ static unsigned int get(unsigned int v, unsigned int (&o)[1]) {
+        o[0] = (v & 0xffffu) << 3;
+        return 0u;
+    }
+};
+template <> struct Fields<FMT_PK2, true> {  // segments A and B; both added to C
+    static constexpr int NF = 2;
+    __device__ __forceinline__ static unsigned int get(unsigned int v, unsigned int (&o)[2]) {
+        o[0] = (v << 3) & 0x1ff8u;
+        o[1] = (v >> 7) & 0x1ff8u;
+        return (v & 0xfff00000u) + ((o[0] + o[1]) << 17);
+    }
+    __device__ __forceinline__ static unsigned int merge(unsigned int first, unsigned int extra) {
+        return first + extra;
+    }
+};
+template <> struct Fields<FMT_PK2, false> {  // C; word cleared
+    static constexpr int NF = 1;
+    __device__ __forceinline__ static unsigned int get(unsigned int v, unsigned int (&o)[1]) {
+        o[0] = (v >> 17) & 0x7ff8u;
+        return 0u;
+    }
+};
+
+// The entropy epilogue: for each of the thread's TPT trials, sum_j T(c_j) over
+// the n phase bins, T(c) = c ln c from the fixed-point table, for every count
+// the word format holds (one, or two segments for FMT_PK2 with SEG).  The
+// trial's counters for the window of logical slots [L, R] start at shared
+// address p0[s] (slot L), `stride` bytes apart; slot L + i counts bin
+// (L + i) mod n, so the first n slots hold one bin each and the
+// e = R - L + 1 - n extra slots L + n + i more points of the bin of slot
+// L + (i mod n) (SPLIT32's two slots per bin).
+// SEG: the counts since the last sweep.  Each extra word is first merged into
+// its bin's first word and cleared, so the sweep proper reads one word per bin;
+// after the last segment every extra word is therefore 0.
+// !SEG: the cumulative counts c_j of the first slots (the marginal term), each
+// word cleared after it is read, so the next work item starts from zero
+// counters without a separate pass.
+// OVL (50 %-overlapping bins, Sec. 2.3): overlapping bin j holds the fine bins j
+// and j + 1 (mod n), so the sum is over T(c_j + c_(j+1)): the first bin is
+// peeled off, each later bin pairs with the one before it, and the last pairs
+// with the first (table offsets add like the counts).  G bins of every trial
+// are loaded before any is stored, so the loads overlap.
+template <int TPT, int FMT, bool SEG, bool ALL_SMEM, bool OVL, int STRIDE>
+struct Sweep {
+    typedef Fields<FMT, SEG> F;
+    static constexpr int NF = F::NF;
+    unsigned int *const cnt;               // the thread's counter words
+    const unsigned long long *const s_tab;  // the c ln c table in shared memory
+    const int table_smem;
+    const unsigned long long *const g_tab;
+    unsigned int first[TPT][NF] = {}, prev[TPT][NF] = {};
+
+    // T(c) for the byte offset o = 8 c
+    __device__ __forceinline__ unsigned long long look(unsigned int o) const {
+        const unsigned long long *e = reinterpret_cast<const unsigned long long *>(
+            reinterpret_cast<const char *>(s_tab) + o);
+        if (ALL_SMEM) return *e;
+        const int c = (int)(o >> 3);
+        return c < table_smem ? *e : __ldg(g_tab + c);
+    }
+
+    // G bins of trial s at words cnt[w[s]], cnt[w[s] + STRIDE], ...; PEEL: the
+    // first bin of an OVL sweep
+    template <int G, bool PEEL>
+    __device__ __forceinline__ void step(int (&w)[TPT], unsigned long long (&acc)[TPT]) {
+        unsigned int v[TPT][G];
 #pragma unroll
         for (int s = 0; s < TPT; ++s)
 #pragma unroll
-            for (int g = 0; g < G; ++g)
+            for (int g = 0; g < G; ++g) v[s][g] = cnt[w[s] + g * STRIDE];
+        unsigned long long t[TPT];
 #pragma unroll
-                for (int k = 0; k < C; ++k) {
-                    p[s][g][k] = wb[s] + (l + off + g + k * n) * stride_j;
-                    v[s][g][k] = *p[s][g][k];
-                }
-        unsigned long long t[TPT][G];
-#pragma unroll
-        for (int s = 0; s < TPT; ++s)
+        for (int s = 0; s < TPT; ++s) {
+            t[s] = 0ull;
 #pragma unroll
             for (int g = 0; g < G; ++g) {
-                unsigned int d = 0u;
+                unsigned int o[NF];
+                v[s][g] = F::get(v[s][g], o);  // v now holds the word to store
 #pragma unroll
-                for (int k = 0; k < C; ++k)
-                    d += SEG ? __byte_perm(v[s][g][k], 0u, 0x1010) - v[s][g][k] : v[s][g][k] << 16;
-                if (OVL) {
-                    if (g == 0 && !started) {  // the first fine bin: kept for the closing pair
-                        first[s] = d;
-                        t[s][g] = 0ull;
+                for (int f = 0; f < NF; ++f) {
+                    if (OVL) {
+                        if (PEEL && g == 0) first[s][f] = o[f];
+                        else t[s] += look(prev[s][f] + o[f]);
+                        prev[s][f] = o[f];
                     } else {
-                        t[s][g] = tab_lookup16<ALL_SMEM>(s_tab, table_smem, g_tab, prev[s] + d);
+                        t[s] += look(o[f]);
                     }
-                    prev[s] = d;
-                } else {
-                    t[s][g] = tab_lookup16<ALL_SMEM>(s_tab, table_smem, g_tab, d);
                 }
             }
-        if (OVL) started = true;
-        if (SEG) {
-#pragma unroll
-            for (int s = 0; s < TPT; ++s)
-#pragma unroll
-                for (int g = 0; g < G; ++g)
-#pragma unroll
-                    for (int k = 0; k < C; ++k) *p[s][g][k] = __byte_perm(v[s][g][k], 0u, 0x1010);
         }
 #pragma unroll
         for (int s = 0; s < TPT; ++s) {
-            unsigned long long sum = t[s][0];
 #pragma unroll
-            for (int g = 1; g < G; ++g) sum += t[s][g];
-            acc[s] += sum;
+            for (int g = 0; g < G; ++g) cnt[w[s] + g * STRIDE] = v[s][g];
+            acc[s] += t[s];
+            w[s] += G * STRIDE;
         }
     }
 
-    __device__ __forceinline__ void sum(int n, int L, int R, unsigned long long (&acc)[TPT]) {
-        const int last = L + n - 1;  // every bin's first slot lies in [L, last]
-        int l = L;
-        if (R - L >= 2 * n) {
-            step<1, 3>(l, n, acc);
-            ++l;
+    // w0[s]: word offset (from cnt) of trial s's first window slot; e: extra
+    // slots (SEG only)
+    __device__ __forceinline__ void run(const int (&w0)[TPT], int n, int e,
+                                        unsigned long long (&acc)[TPT]) {
+        if (SEG) {
+            for (int i = 0, b = 0; i < e; ++i, b = (b + 1 == n) ? 0 : b + 1) {
+#pragma unroll
+                for (int s = 0; s < TPT; ++s) {
+                    unsigned int *q = cnt + w0[s] + (n + i) * STRIDE;
+                    unsigned int *f = cnt + w0[s] + b * STRIDE;
+                    const unsigned int x = *q;
+                    *q = 0u;
+                    *f = merge(*f, x);
+                }
+            }
         }
-        // about four counters in flight per step
-        constexpr int GP = TPT == 1 ? 2 : 1, GS = TPT == 1 ? 4 : 2;
-        const int pe = min(R - n, last);
-        for (; l + GP - 1 <= pe; l += GP) step<GP, 2>(l, n, acc);
-        for (; l <= pe; ++l) step<1, 2>(l, n, acc);
-        for (; l + GS - 1 <= last; l += GS) step<GS, 1>(l, n, acc);
-        for (; l <= last; ++l) step<1, 1>(l, n, acc);
+        int w[TPT];
+#pragma unroll
+        for (int s = 0; s < TPT; ++s) w[s] = w0[s];
+        constexpr int G = TPT * NF >= 4 ? 2 : 4;
+        int j = 0;
+        if (OVL) {
+            step<1, true>(w, acc);
+            j = 1;
+        }
+        for (; j + G <= n; j += G) step<G, false>(w, acc);
+        if (G > 2 && (n - j) >= 2) {
+            step<2, false>(w, acc);
+            j += 2;
+        }
+        if (j < n) step<1, false>(w, acc);
         if (OVL) {
 #pragma unroll
             for (int s = 0; s < TPT; ++s)
-                acc[s] += tab_lookup<ALL_SMEM>(s_tab, table_smem, g_tab, (int)((prev[s] + first[s]) >> 16));
+#pragma unroll
+                for (int f = 0; f < NF; ++f) acc[s] += look(prev[s][f] + first[s][f]);
+        }
+    }
+
+  private:
+    template <bool S = SEG>
+    __device__ __forceinline__ static unsigned int merge(unsigned int w, unsigned int x) {
+        if constexpr (S) return F::merge(w, x);
+        else return w;
+    }
+};
+
+// Dispatch of the sweeps of one work item over the run-time choices (overlapping
+// bins, whole table in shared memory).
+template <int TPT, int STRIDE>
+struct Sweeper {
+    unsigned int *cnt;
+    const unsigned long long *s_tab;
+    int table_smem;
+    const unsigned long long *g_tab;
+    int n;  // phase bins
+
+    template <int FMT>
+    __device__ __forceinline__ void segment(bool ovl, bool tab_all, const int (&w0)[TPT], int e,
+                                            unsigned long long (&acc)[TPT]) const {
+        if (ovl) {
+            if (tab_all) Sweep<TPT, FMT, true, true, true, STRIDE>{cnt, s_tab, table_smem, g_tab}.run(w0, n, e, acc);
+            else Sweep<TPT, FMT, true, false, true, STRIDE>{cnt, s_tab, table_smem, g_tab}.run(w0, n, e, acc);
+        } else {
+            if (tab_all) Sweep<TPT, FMT, true, true, false, STRIDE>{cnt, s_tab, table_smem, g_tab}.run(w0, n, e, acc);
+            else Sweep<TPT, FMT, true, false, false, STRIDE>{cnt, s_tab, table_smem, g_tab}.run(w0, n, e, acc);
+        }
+    }
+    template <int FMT>
+    __device__ __forceinline__ void marginal(bool ovl, bool tab_all, const int (&w0)[TPT],
+                                             unsigned long long (&acc)[TPT]) const {
+        if (ovl) {
+            if (tab_all) Sweep<TPT, FMT, false, true, true, STRIDE>{cnt, s_tab, table_smem, g_tab}.run(w0, n, 0, acc);
+            else Sweep<TPT, FMT, false, false, true, STRIDE>{cnt, s_tab, table_smem, g_tab}.run(w0, n, 0, acc);
+        } else {
+            if (tab_all) Sweep<TPT, FMT, false, true, false, STRIDE>{cnt, s_tab, table_smem, g_tab}.run(w0, n, 0, acc);
+            else Sweep<TPT, FMT, false, false, false, STRIDE>{cnt, s_tab, table_smem, g_tab}.run(w0, n, 0, acc);
         }
     }
 };
@@ -351,6 +441,7 @@ struct BinWindow {
 __device__ __forceinline__ float split_fh(const float4 &t) { return t.x; }
 template <class T>
 __device__ __forceinline__ float split_fh(const T &) { return 0.0f; }
+
 
 // The slots a SPLIT32 fold can reach.  The fold's residual x obeys |x| <=
 // 1/2 + 2^-23 |th fh| (1 + 2^-22) + 2^-23 without the Pdot term (the two
@@ -388,12 +479,12 @@ __device__ __forceinline__ void chan_merge(double &n, double &mean, double &m2, 
 // memory to about three 256-thread CTAs per SM at 15 phase bins, so those
 // kernels take the registers that frees (80 at 256 threads) instead of 64.
 // Four trials per thread need four times the counters of one: at most 512
-// threads per SM fit, and those kernels take up to 128 registers.
+// threads per SM fit, and those kernels take up to 128 registers.  One trial
+// per thread is the shape for many phase bins (50 and up), where the counters
+// again leave room for about 512 threads per SM: 128 registers as well.
 constexpr int main_min_blocks(int tpt, int log2b) {
-    return tpt == 4 ? (log2b >= 9 ? 1 : (log2b == 8 ? 2 : (log2b == 7 ? 4 : 8)))
-           : tpt == 2
-               ? (log2b >= 9 ? 2 : (log2b == 8 ? 3 : (log2b == 7 ? 6 : 8)))
-               : (log2b >= 9 ? 2 : (log2b == 8 ? 4 : 8));
+    return tpt == 2 ? (log2b >= 9 ? 2 : (log2b == 8 ? 3 : (log2b == 7 ? 6 : 8)))
+                    : (log2b >= 9 ? 1 : (log2b == 8 ? 2 : (log2b == 7 ? 4 : 8)));
 }
 
 template <int MODE, int TPT, int LOG2B>
@@ -417,9 +508,11 @@ __global__ void __launch_bounds__(1 << LOG2B, main_min_blocks(TPT, LOG2B)) k_mai
     const int slot_off = -zr.zmin;  // physical index of logical slot l: l + slot_off
     const int stride_j = B, stride_s = n_slots * B;
 
-    point_t *s_pts = reinterpret_cast<point_t *>(smem);
-    unsigned long long *s_tab = reinterpret_cast<unsigned long long *>(s_pts + a.chunk);
-    unsigned int *s_cnt = reinterpret_cast<unsigned int *>(s_tab + a.table_smem);
+    // the table first (its address is then a constant), padded to an even count
+    // so that the staged points after it stay 16-byte aligned
+    unsigned long long *s_tab = reinterpret_cast<unsigned long long *>(smem);
+    point_t *s_pts = reinterpret_cast<point_t *>(s_tab + ((a.table_smem + 1) & ~1));
+    unsigned int *s_cnt = reinterpret_cast<unsigned int *>(s_pts + a.chunk);
     int *s_seg = reinterpret_cast<int *>(s_cnt + TPT * n_slots * B);
     unsigned long long *s_top =
         reinterpret_cast<unsigned long long *>(s_seg + ((n_mag + 2) & ~1));
@@ -430,6 +523,9 @@ __global__ void __launch_bounds__(1 << LOG2B, main_min_blocks(TPT, LOG2B)) k_mai
     const point_t *g_pts = reinterpret_cast<const point_t *>(a.payload);
     const trial_t *g_tr = reinterpret_cast<const trial_t *>(a.trialc);
     unsigned int *my_cnt = s_cnt + tid;
+    // counters start at zero; every work item's final sweep clears the words it
+    // used, so later items start from zero as well
+    for (int i = 0; i < TPT * n_slots; ++i) my_cnt[i * B] = 0u;
 #if defined(GCE_CHECK_SLOTS)
     FoldConst fk = fold_const(n_phase);
     fk.zmin = zr.zmin;
@@ -451,6 +547,16 @@ __global__ void __launch_bounds__(1 << LOG2B, main_min_blocks(TPT, LOG2B)) k_mai
         SPLIT ? __double2float_ru(__longlong_as_double((long long)a.state->tau_max_bits)) : 0.0f;
 
     int staged_curve = -1, staged_lo = -1;
+    // the tile whose trial constants, flags and counter window are loaded: work
+    // items of the same tile reuse them
+    int cur_tile = -1;
+    typename Fold<MODE>::prep_t tc[TPT];
+    long long tt[TPT];
+    bool pdot = false, k0 = true;
+    const bool pdm = a.pd_major != 0;
+    int wl[TPT];           // word offset (from my_cnt) of each trial's first window slot
+
+    int n_extra = 0;       // window slots beyond n_phase
     long long item = 0, item_end = 0;
     for (;;) {
         if (item >= item_end) {
@@ -461,8 +567,18 @@ __global__ void __launch_bounds__(1 << LOG2B, main_min_blocks(TPT, LOG2B)) k_mai
             item_end = min(item + (long long)a.grab, a.n_items);
             if (item >= a.n_items) break;
         }
-        const int ci = (int)(item / a.n_tiles);
-        const int tile = (int)(item - (long long)ci * a.n_tiles);
+        // items [0, n_long_items) run curve-major over the long curves (consecutive
+        // items share the staged curve); the rest tile-major over the short curves
+        // at the end of the order (consecutive items share the tile's trials)
+        int ci, tile;
+        if (item < a.n_long_items) {
+            ci = (int)(item / a.n_tiles);
+            tile = (int)(item - (long long)ci * a.n_tiles);
+        } else {
+            const long long j = item - a.n_long_items;
+            tile = (int)(j / a.n_short);
+            ci = a.n_long + (int)(j - (long long)tile * a.n_short);
+        }
         const int c = a.order[ci];
         const long long off = a.offsets[c];
         const int n = (int)(a.offsets[c + 1] - off);
@@ -474,55 +590,72 @@ __global__ void __launch_bounds__(1 << LOG2B, main_min_blocks(TPT, LOG2B)) k_mai
             staged_lo = -1;
         }
 
-        typename Fold<MODE>::prep_t tc[TPT];
-        long long tt[TPT];
-        bool any_pdot = false, all_k0 = true;
-        // trial indices (n_trials marks a slot past the grid): a run of B x TPT
-        // flat indices, or B periods x TPT Pdot values (period-major tiles)
-        const bool pdm = a.pd_major != 0;
-        long long p_idx = 0;
-        int q_base = 0;
-        if (pdm) {
-            p_idx = (long long)(tile % a.n_ptiles) * B + tid;
-            q_base = (tile / a.n_ptiles) * TPT;
-        }
-#pragma unroll
-        for (int s = 0; s < TPT; ++s) {
-            if (pdm)
-                tt[s] = (p_idx < a.n_periods && q_base + s < a.n_pdots)
-                            ? (long long)(q_base + s) * a.n_periods + p_idx
-                            : a.n_trials;
-            else
-                tt[s] = (long long)tile * (B * TPT) + (long long)s * B + tid;
-            trial_t tr{};
-            if (tt[s] < a.n_trials) {
-                tr = g_tr[tt[s]];
-                any_pdot |= Fold<MODE>::has_pdot(tr);
+        if (tile != cur_tile) {
+            cur_tile = tile;
+            bool any_pdot = false, all_k0 = true;
+            // trial indices (n_trials marks a slot past the grid): a run of B x TPT
+            // flat indices, or B periods x TPT Pdot values (period-major tiles)
+            long long p_idx = 0;
+            int q_base = 0;
+            if (pdm) {
+                p_idx = (long long)(tile % a.n_ptiles) * B + tid;
+                q_base = (tile / a.n_ptiles) * TPT;
             }
-            tc[s] = Fold<MODE>::prepare(tr);
-            all_k0 &= Fold<MODE>::k_zero(tc[s]);
-        }
-        const bool pdot = __syncthreads_or(any_pdot) != 0;
-        const bool k0 = MODE != GCE_PHASE_FIXED32 || __syncthreads_and(all_k0) != 0;
-        // live logical slots [L, R] of this warp's counters (warp-uniform)
-        int L = 0, R = n_phase - 1;
-        if (SPLIT) {
-            float fm = 0.0f;
 #pragma unroll
-            for (int s = 0; s < TPT; ++s)
-                if (tt[s] < a.n_trials) fm = fmaxf(fm, fabsf(split_fh(tc[s])));
-            fm = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(fm)));
-            int zlo, zhi;
-            split_slot_window(pdot || narrow, tau_max_f * fm, n_phase, zlo, zhi);
-            L = max(zlo, zr.zmin);
-            R = min(zhi, zr.zmax);
+            for (int s = 0; s < TPT; ++s) {
+                if (pdm)
+                    tt[s] = (p_idx < a.n_periods && q_base + s < a.n_pdots)
+                                ? (long long)(q_base + s) * a.n_periods + p_idx
+                                : a.n_trials;
+                else
+                    tt[s] = (long long)tile * (B * TPT) + (long long)s * B + tid;
+                trial_t tr{};
+                if (tt[s] < a.n_trials) {
+                    tr = g_tr[tt[s]];
+                    any_pdot |= Fold<MODE>::has_pdot(tr);
+                }
+                tc[s] = Fold<MODE>::prepare(tr);
+                all_k0 &= Fold<MODE>::k_zero(tc[s]);
+            }
+            pdot = __syncthreads_or(any_pdot) != 0;
+            k0 = MODE != GCE_PHASE_FIXED32 || __syncthreads_and(all_k0) != 0;
+            // live logical slots [L, R] of this warp's counters (warp-uniform)
+            int L = 0, R = n_phase - 1;
+            if (SPLIT) {
+                float fm = 0.0f;
+#pragma unroll
+                for (int s = 0; s < TPT; ++s)
+                    if (tt[s] < a.n_trials) fm = fmaxf(fm, fabsf(split_fh(tc[s])));
+                fm = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(fm)));
+                int zlo, zhi;
+                split_slot_window(pdot || narrow, tau_max_f * fm, n_phase, zlo, zhi);
+                L = max(zlo, zr.zmin);
+                R = min(zhi, zr.zmax);
+            }
+#pragma unroll
+            for (int s = 0; s < TPT; ++s) wl[s] = s * stride_s + (L + slot_off) * stride_j;
+            n_extra = R - L + 1 - n_phase;
+
+#if defined(GCE_CHECK_SLOTS)
+            // checked builds: every increment must also lie in the warp's window
+            fk.zmin = L;
+            fk.zmax = R;
+#endif
         }
 
-        for (int i = 0; i < TPT * n_slots; ++i) my_cnt[i * B] = 0u;
         unsigned long long s_ij[TPT];
 #pragma unroll
         for (int s = 0; s < TPT; ++s) s_ij[s] = 0ull;
 
+        // FMT_PK2 (one sweep per two non-empty segments) with 50 %-overlapping
+        // bins on curves of at most kPk2MaxN points, else FMT_SNAP (one sweep per
+        // segment).  Each count costs the same table lookup and 64-bit add in both
+        // formats; FMT_PK2 saves the loads, stores and the overlapping pairs' set-up
+        // of every other sweep, which pays with overlapping bins and costs more
+        // field arithmetic than it saves without them.
+        const bool pk2 = ovl && n <= kPk2MaxN;
+        const Sweeper<TPT, B> sw{my_cnt, s_tab, a.table_smem, a.table, n_phase};
+        int ended = 0;  // non-empty segments ended so far (FMT_PK2: field = ended & 1)
         for (int lo = 0; lo < n; lo += a.chunk) {
             const int hi = min(n, lo + a.chunk);
             if (staged_lo != lo) {
@@ -536,50 +669,40 @@ __global__ void __launch_bounds__(1 << LOG2B, main_min_blocks(TPT, LOG2B)) k_mai
                 const int s0 = s_seg[i], s1 = s_seg[i + 1];
                 const int ka = max(s0, lo), kb = min(s1, hi);
                 if (ka < kb) {
+                    const unsigned int inc = (pk2 && (ended & 1)) ? kPk2IncB : 1u;
                     compiler_fence();
                     const typename ModeTraits<MODE>::point_t *pp = s_pts;
                     if (k0) {
-                        if (pdot) count_points_any<MODE, TPT, SH, true, true>(pdm, pp, ka - lo, kb - lo, tc, base, fk);
-                        else if (SPLIT && narrow) count_points_any<MODE, TPT, SH, false, true, SPLIT>(pdm, pp, ka - lo, kb - lo, tc, base, fk);
-                        else count_points_any<MODE, TPT, SH, false, true>(pdm, pp, ka - lo, kb - lo, tc, base, fk);
+                        if (pdot) count_points_any<MODE, TPT, SH, true, true>(pdm, pp, ka - lo, kb - lo, tc, base, fk, inc);
+                        else if (SPLIT && narrow) count_points_any<MODE, TPT, SH, false, true, SPLIT>(pdm, pp, ka - lo, kb - lo, tc, base, fk, inc);
+                        else count_points_any<MODE, TPT, SH, false, true>(pdm, pp, ka - lo, kb - lo, tc, base, fk, inc);
                     } else if (MODE == GCE_PHASE_FIXED32) {
-                        if (pdot) count_points_any<MODE, TPT, SH, true, false>(pdm, pp, ka - lo, kb - lo, tc, base, fk);
-                        else count_points_any<MODE, TPT, SH, false, false>(pdm, pp, ka - lo, kb - lo, tc, base, fk);
+                        if (pdot) count_points_any<MODE, TPT, SH, true, false>(pdm, pp, ka - lo, kb - lo, tc, base, fk, inc);
+                        else count_points_any<MODE, TPT, SH, false, false>(pdm, pp, ka - lo, kb - lo, tc, base, fk, inc);
                     }
                     compiler_fence();
                 }
                 if (s1 > s0 && s1 > lo && s1 <= hi) {
-                    // end of magnitude segment i: c_ij = counter - snapshot
-                    if (ovl) {
-                        if (tab_all)
-                            BinWindow<TPT, true, true, true>{wbase, slot_off, stride_j, s_tab, a.table_smem, a.table}
-                                .sum(n_phase, L, R, s_ij);
-                        else
-                            BinWindow<TPT, true, false, true>{wbase, slot_off, stride_j, s_tab, a.table_smem, a.table}
-                                .sum(n_phase, L, R, s_ij);
-                    } else {
-                        if (tab_all)
-                            BinWindow<TPT, true, true, false>{wbase, slot_off, stride_j, s_tab, a.table_smem, a.table}
-                                .sum(n_phase, L, R, s_ij);
-                        else
-                            BinWindow<TPT, true, false, false>{wbase, slot_off, stride_j, s_tab, a.table_smem, a.table}
-                                .sum(n_phase, L, R, s_ij);
-                    }
+                    // end of non-empty magnitude segment i: sweep its counts (FMT_PK2:
+                    // after every second one)
+                    if (!pk2) sw.segment<FMT_SNAP>(ovl, tab_all, wl, n_extra, s_ij);
+                    else if (ended & 1) sw.segment<FMT_PK2>(ovl, tab_all, wl, n_extra, s_ij);
+                    ++ended;
                 }
             }
         }
+        if (pk2 && (ended & 1)) sw.segment<FMT_PK2>(ovl, tab_all, wl, n_extra, s_ij);  // the last, alone
 
         // sum_j c_j ln c_j from the cumulative counters, then H (the counts total
-        // 2N with overlapping bins, every point being in two bins)
+        // 2N with overlapping bins, every point being in two bins); this sweep
+        // clears the counters for the next item (the extra slots are already 0)
         const double inv = kTabInvScale / (double)(n * (1 + ovl));
         unsigned long long key[TPT], sjs[TPT];
         float hv[TPT];
 #pragma unroll
         for (int s = 0; s < TPT; ++s) sjs[s] = 0ull;
-        if (ovl)
-            BinWindow<TPT, false, false, true>{wbase, slot_off, stride_j, s_tab, a.table_smem, a.table}.sum(n_phase, L, R, sjs);
-        else
-            BinWindow<TPT, false, false, false>{wbase, slot_off, stride_j, s_tab, a.table_smem, a.table}.sum(n_phase, L, R, sjs);
+        if (pk2) sw.marginal<FMT_PK2>(ovl, tab_all, wl, sjs);
+        else sw.marginal<FMT_SNAP>(ovl, tab_all, wl, sjs);
 #pragma unroll
         for (int s = 0; s < TPT; ++s) {
             const unsigned long long sj = sjs[s];
@@ -830,7 +953,7 @@ cudaError_t launch_for_block(int block, int grid, size_t smem, const MainArgs &a
 size_t main_smem_bytes(int mode, int block, int tpt, int chunk, int n_phase, int n_mag,
                        int table_smem, int k, int narrow) {
     size_t pt = mode == GCE_PHASE_FP64 ? 8 : 16;
-    size_t b = pt * (size_t)chunk + 8 * (size_t)table_smem +
+    size_t b = 8 * (size_t)((table_smem + 1) & ~1) + pt * (size_t)chunk +
                4 * (size_t)tpt * slots_per_trial(mode, n_phase, narrow != 0) * block +
                4 * (size_t)((n_mag + 2) & ~1) + 8 * (size_t)(block / 32) * (size_t)(k > 0 ? k : 1) +
                24 * (size_t)(block / 32);
@@ -853,10 +976,28 @@ const void *main_kernel_ptr(int mode, int tpt, int block) {
     }
 }
 
-cudaError_t main_kernel_attrs(int mode, int tpt, int block, size_t smem) {
+// The kernel's dynamic shared-memory limit is raised to the device's opt-in
+// maximum, never set to one job's size, so that calls planned on other host
+// threads (which all set the same value) cannot lower it between their planning
+// and their launch.
+// The dynamic shared memory a CTA of the kernel can have: the device's opt-in
+// maximum less the kernel's static shared memory (0 if the kernel is unknown).
+size_t main_dynamic_smem_limit(int mode, int tpt, int block, size_t smem_optin) {
+    const void *f = main_kernel_ptr(mode, tpt, block);
+    cudaFuncAttributes fa;
+    if (!f || cudaFuncGetAttributes(&fa, f) != cudaSuccess || fa.sharedSizeBytes > smem_optin) {
+        cudaGetLastError();
+        return 0;
+    }
+    return smem_optin - fa.sharedSizeBytes;
+}
+
+cudaError_t main_kernel_attrs(int mode, int tpt, int block, size_t smem_optin) {
     const void *f = main_kernel_ptr(mode, tpt, block);
     if (!f) return cudaErrorInvalidValue;
-    return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t lim = main_dynamic_smem_limit(mode, tpt, block, smem_optin);
+    if (lim == 0) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim);
 }
 
 cudaError_t launch_main(int mode, int tpt, int block, int grid, size_t smem, const MainArgs &a,

@@ -237,6 +237,9 @@ extern "C" gce_status gce_ce_topk_static(const double *times, const double *mags
     ma.pd_major = tg.pd_major;
     ma.narrow = narrow;
     ma.n_items = n_items;
+    ma.n_long_items = n_items;  // every curve curve-major
+    ma.n_long = n_curves;
+    ma.n_short = 0;
     ma.grab = 1;
     ma.n_phase = cfg->n_phase_bins;
     ma.n_mag = cfg->n_mag_bins;
