@@ -96,7 +96,7 @@ def profiled_traffic(mode, workload, n_curves):
             k, v = line.split(":", 1)
             rec[k.strip()] = v.strip()
     h = hashlib.sha256()
-    for f in ("gce_main.cu", "gce_internal.cuh"):
+    for f in ("gce_kernel.cuh", "gce_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2006_06866_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     if rec.get("kernel_sources_sha256_16") != h.hexdigest()[:16]:

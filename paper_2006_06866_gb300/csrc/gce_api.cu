@@ -310,7 +310,7 @@ struct Job {
 struct Plan {
     long long n_points, n_trials, n_items, n_long_items;
     int n_long, n_short;  // curves taken curve-major / tile-major (see MainArgs)
-    int n_max, n_tiles, n_ptiles, pd_major, narrow, block, tpt, grid, chunk, table_smem, grab;
+    int n_max, n_tiles, n_ptiles, pd_major, narrow, half, block, tpt, grid, chunk, table_smem, grab;
     int n_groups, tiles_per_group;  // top-k: first merge level (0 groups: none)
     size_t smem;
 };
@@ -329,8 +329,12 @@ gce_status make_plan(gce_handle h, const Job &j, Plan &pl) {
     const int kk = j.kind == JOB_TOPK ? j.k : 0;
     // a Pdot axis: SPLIT32 keeps the narrow slot range (every fold re-reduced)
     pl.narrow = (cfg->phase_mode == GCE_PHASE_SPLIT32 && j.n_pdots > 1) ? 1 : 0;
+    // one Pdot value: the SPLIT32 / FIXED32 staging holds 8-byte half points
+    pl.half = (cfg->phase_mode != GCE_PHASE_FP64 && j.n_pdots == 1) ? 1 : 0;
+    const bool ovl = (cfg->flags & GCE_FLAG_OVERLAP) != 0;  // a kernel of its own
     const ShapeKey skey(cfg->phase_mode, cfg->n_phase_bins, cfg->n_mag_bins, pl.n_max, kk,
-                        pl.narrow, t.block, t.tpt, t.chunk, t.ctas_per_sm);
+                        pl.narrow * 4 + pl.half * 2 + (ovl ? 1 : 0), t.block, t.tpt, t.chunk,
+                        t.ctas_per_sm);
     int occ = 0;
     auto sit = h->shapes.find(skey);
     if (sit != h->shapes.end()) {
@@ -353,10 +357,10 @@ gce_status make_plan(gce_handle h, const Job &j, Plan &pl) {
         // block, until the CTA fits in shared memory
         auto size = [&]() {
             return main_smem_bytes(cfg->phase_mode, pl.block, pl.tpt, pl.chunk, cfg->n_phase_bins,
-                                   cfg->n_mag_bins, pl.table_smem, kk, pl.narrow);
+                                   cfg->n_mag_bins, pl.table_smem, kk, pl.narrow, pl.half);
         };
         auto limit = [&]() {
-            return main_dynamic_smem_limit(cfg->phase_mode, pl.tpt, pl.block, (size_t)h->smem_optin);
+            return main_dynamic_smem_limit(cfg->phase_mode, pl.tpt, pl.block, ovl, (size_t)h->smem_optin);
         };
         pl.smem = size();
         while (pl.smem > limit()) {
@@ -370,8 +374,8 @@ gce_status make_plan(gce_handle h, const Job &j, Plan &pl) {
         }
         if (pl.smem > limit())
             return fail(h, GCE_ERR_UNSUPPORTED, "launch shape needs %zu bytes of shared memory", pl.smem);
-        CUDA_TRY(h, main_kernel_attrs(cfg->phase_mode, pl.tpt, pl.block, (size_t)h->smem_optin));
-        const void *kern = main_kernel_ptr(cfg->phase_mode, pl.tpt, pl.block);
+        CUDA_TRY(h, main_kernel_attrs(cfg->phase_mode, pl.tpt, pl.block, ovl, (size_t)h->smem_optin));
+        const void *kern = main_kernel_ptr(cfg->phase_mode, pl.tpt, pl.block, ovl);
         CUDA_TRY(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, pl.block, pl.smem));
         if (occ < 1) return fail(h, GCE_ERR_UNSUPPORTED, "launch shape does not fit on an SM");
         // A smaller staged chunk costs only more staging passes: take it whenever it
@@ -503,6 +507,7 @@ gce_status enqueue(gce_handle h, const Job &j, const Plan &pl, cudaStream_t s, b
     ma.k = 0;
     ma.stats = nullptr;
     ma.overlap = (cfg->flags & GCE_FLAG_OVERLAP) ? 1 : 0;
+    ma.half = pl.half;
     ma.state = st;
     const bool timed = (cfg->flags & GCE_FLAG_TIME_KERNEL) != 0;
     gce_status ms;

@@ -77,17 +77,25 @@ struct FixedTrial {
     float4 f;  // {G0, G2, K, k as bits}: the FP32 cross terms' scales and offset
 };
 template <int MODE> struct ModeTraits;
+// half_t: the first two words of a point, all a fold without a Pdot term reads
+// (SPLIT32 {tau_hi, tau_lo}, FIXED32 {T1, t0f}); FP64 points are one word.
 template <> struct ModeTraits<GCE_PHASE_FP64> {
     typedef double point_t;
+    typedef double half_t;
     typedef double2 trial_t;
+    __device__ static point_t widen(half_t h) { return h; }
 };
 template <> struct ModeTraits<GCE_PHASE_SPLIT32> {
     typedef float4 point_t;
+    typedef float2 half_t;
     typedef float4 trial_t;
+    __device__ static point_t widen(half_t h) { return make_float4(h.x, h.y, 0.0f, 0.0f); }
 };
 template <> struct ModeTraits<GCE_PHASE_FIXED32> {
     typedef uint4 point_t;
+    typedef uint2 half_t;
     typedef FixedTrial trial_t;
+    __device__ static point_t widen(half_t h) { return make_uint4(h.x, h.y, 0u, 0u); }
 };
 
 // Balanced split of a 64-bit value: x = hi 2^32 + lo with lo a signed 32-bit
@@ -301,6 +309,31 @@ __host__ __device__ inline int slots_per_trial(int mode, int n_phase, bool narro
     return r.zmax - r.zmin + 1;
 }
 
+// Byte offsets of the CE kernel's dynamic shared-memory regions, in order: the
+// c ln c table (an even number of 8-byte entries, so the points after it stay
+// 16-byte aligned), the staged points (8 bytes each for FP64 and for half
+// points, else 16; chunk is a multiple of 32), the counters, the segment starts
+// (an even count, so the 8-byte keys after them stay aligned), the top-k keys
+// and the moments.  The host sizes the launch with `total` and the kernel
+// carves its memory with the same offsets.
+struct MainSmemLayout {
+    unsigned int pts, cnt, seg, top, stat, total;
+};
+__host__ __device__ inline MainSmemLayout main_smem_layout(int mode, int block, int tpt, int chunk,
+                                                           int n_phase, int n_mag,
+                                                           int table_smem, int k, int narrow,
+                                                           int half) {
+    MainSmemLayout L;
+    const unsigned int pt = (mode == GCE_PHASE_FP64 || half) ? 8u : 16u;
+    L.pts = 8u * (unsigned int)((table_smem + 1) & ~1);
+    L.cnt = L.pts + pt * (unsigned int)chunk;
+    L.seg = L.cnt + 4u * (unsigned int)(tpt * slots_per_trial(mode, n_phase, narrow != 0) * block);
+    L.top = L.seg + 4u * (unsigned int)((n_mag + 2) & ~1);
+    L.stat = L.top + 8u * (unsigned int)((block / 32) * (k > 0 ? k : 1));
+    L.total = L.stat + 24u * (unsigned int)(block / 32);
+    return L;
+}
+
 // Fixed-point table of c ln c: tab[c] = round(c ln(c) 2^32), tab[0] = tab[1] = 0.
 // Eq. 4 rewritten with integer counts is
 //   N H = sum_j c_j ln c_j - sum_ij c_ij ln c_ij,
@@ -391,6 +424,10 @@ struct MainArgs {
     int k;
     TileStats *stats;          // per-tile moments [n_curves][n_tiles] or nullptr
     int overlap;               // 50 %-overlapping phase bins
+    // SPLIT32 / FIXED32 with one Pdot value: the staging buffer holds `chunk`
+    // half points (8 bytes); a job whose Pdot is 0 stages half points, one whose
+    // single Pdot is not 0 stages chunk / 2 whole points in the same bytes
+    int half;
     JobState *state;
 };
 
@@ -406,11 +443,21 @@ cudaError_t launch_band_stats(const double *mags, const unsigned char *bands,
                               double2 *stats, JobState *st, cudaStream_t s);
 cudaError_t launch_table(unsigned long long *table, int n_max, cudaStream_t s);
 size_t main_smem_bytes(int mode, int block, int tpt, int chunk, int n_phase, int n_mag,
-                       int table_smem, int k, int narrow);
+                       int table_smem, int k, int narrow, int half);
 size_t single_smem_bytes(int n_phase, int block);
-size_t main_dynamic_smem_limit(int mode, int tpt, int block, size_t smem_optin);
-cudaError_t main_kernel_attrs(int mode, int tpt, int block, size_t smem_optin);
-const void *main_kernel_ptr(int mode, int tpt, int block);
+size_t main_dynamic_smem_limit(int mode, int tpt, int block, bool ovl, size_t smem_optin);
+cudaError_t main_kernel_attrs(int mode, int tpt, int block, bool ovl, size_t smem_optin);
+const void *main_kernel_ptr(int mode, int tpt, int block, bool ovl);
+// per fold mode (gce_main_<mode>.cu)
+const void *main_kernel_ptr_fp64(int tpt, int block, bool ovl);
+const void *main_kernel_ptr_split32(int tpt, int block, bool ovl);
+const void *main_kernel_ptr_fixed32(int tpt, int block, bool ovl);
+cudaError_t launch_main_fp64(int tpt, int block, int grid, size_t smem, const MainArgs &a,
+                             cudaStream_t s);
+cudaError_t launch_main_split32(int tpt, int block, int grid, size_t smem, const MainArgs &a,
+                                cudaStream_t s);
+cudaError_t launch_main_fixed32(int tpt, int block, int grid, size_t smem, const MainArgs &a,
+                                cudaStream_t s);
 cudaError_t launch_main(int mode, int tpt, int block, int grid, size_t smem,
                         const MainArgs &a, cudaStream_t s);
 cudaError_t launch_topk_merge(const unsigned long long *cand, int n_curves, int n_tiles,

@@ -1,793 +1,12 @@
-// The CE hot path: fold (Eq. 3) -> phase x magnitude histogram (Sec. 2.3) ->
-// entropy (Eq. 4) -> grid or per-curve top-k (Sec. 2.3, Sec. 4).
-//
-// Work decomposition.  One thread owns TPT trials (P, Pdot) of one light curve
-// -- the paper's thread-per-grid-point design (Sec. 2.3.2) -- and a CTA owns a
-// tile of block * TPT consecutive flat trial indices.  A work item is one
-// (curve, tile) pair; CTAs are persistent and take items from one atomic
-// counter, longest curves first.  The curve's points, regrouped by magnitude
-// bin during preparation, are staged in shared memory and read by every thread
-// as broadcasts.  Because the points arrive one magnitude bin at a time, each
-// thread needs only a 1-D phase histogram per trial (the paper's
-// 1/n_mag-memory observation).
-//
-// Counters.  One 32-bit shared-memory word per (trial, phase slot), private to
-// its thread and laid out [trial][slot][thread] so a warp's accesses fall in
-// distinct banks.  The low 16 bits count points (N <= 65535); the high 16 bits
-// hold a snapshot taken at the end of the previous magnitude segment, so the
-// segment's c_ij is low - high.  Points are counted with a shared-memory atomic
-// add whose result is unused: it needs no read-modify-write round trip in the
-// thread, and no other thread touches the word.
-//
-// Entropy.  N H = sum_j c_j ln c_j - sum_ij c_ij ln c_ij, accumulated as exact
-// 64-bit integers from a fixed-point c ln c table (2^32 scale); H is converted
-// to float32 once per trial.
-#include <cmath>
-#include <cstdint>
-
-#include "gce_internal.cuh"
+// The kernels around the CE kernel: per-curve top-k merge (and the Eq. 5
+// moments), the plain one-launch-per-curve FP64 baseline, diagnostic counts,
+// and the dispatch of the CE kernel's instantiations (one translation unit per
+// fold mode: gce_main_fp64.cu, gce_main_split32.cu, gce_main_fixed32.cu).
+#include "gce_kernel.cuh"
 
 namespace gce {
 
 namespace {
-
-constexpr unsigned long long kNoKey = ~0ull;
-
-// Warp minimum of (H bits, trial index) keys by two single-instruction warp
-// reductions: the smallest high word, then the smallest low word among the
-// lanes holding it (the same order as the 64-bit key).
-__device__ __forceinline__ unsigned long long warp_min_key(unsigned long long v) {
-    const unsigned int hi = (unsigned int)(v >> 32);
-    const unsigned int mh = __reduce_min_sync(0xffffffffu, hi);
-    const unsigned int ml = __reduce_min_sync(0xffffffffu, hi == mh ? (unsigned int)v : 0xffffffffu);
-    return ((unsigned long long)mh << 32) | ml;
-}
-
-
-// Per-mode constants of the fold, computed once per kernel.
-struct FoldConst {
-    double nphi_d;
-    float nphi_f;
-    float zoff;          // SPLIT32: 1.5 2^23 + n_phase
-    int n_phase;
-#if defined(GCE_CHECK_SLOTS)
-    // checked builds: the trial's kept logical slots and where to flag a miss
-    int zmin, zmax;
-    unsigned int *err;
-#endif
-};
-
-__device__ __forceinline__ FoldConst fold_const(int n_phase) {
-    FoldConst k;
-    k.nphi_d = (double)n_phase;
-    k.nphi_f = (float)n_phase;
-    k.zoff = kRound + (float)n_phase;
-    k.n_phase = n_phase;
-    return k;
-}
-
-// Fold<MODE> turns a trial's stored constants into the registers its fold
-// needs (prepare) and folds one point into a raw counter slot: the phase bin
-// (FP64, FIXED32) or, for SPLIT32, the bit pattern of the rounding FMA, whose
-// offset kSlotBias is removed once from the counter base address instead of
-// per point.  raw - kSlotBias is the bin, or for SPLIT32 the bin or the bin
-// plus n_phase (two slots per bin).
-// fpart / offset_from split the fold at its period part (what trials of the same
-// period share); offset is the two composed, so every path folds identically.
-template <int MODE> struct Fold;
-template <> struct Fold<GCE_PHASE_FP64> {
-    typedef double2 prep_t;
-    typedef double fpart_t;
-    static constexpr int kSlotBias = 0;
-    __device__ __forceinline__ static prep_t prepare(double2 t) { return t; }
-    template <bool PDOT>
-    __device__ __forceinline__ static int raw_slot(double p, const prep_t &t, const FoldConst &k) {
-        return fold_fp64<PDOT>(p, t.x, t.y, k.nphi_d, k.n_phase);
-    }
-    __device__ __forceinline__ static fpart_t fpart(double p, const prep_t &t) {
-        return fold_fp64_fpart(p, t.x);
-    }
-    template <bool PDOT, bool K0, int SH, bool RED>
-    __device__ __forceinline__ static unsigned int offset_from(fpart_t f, double p,
-                                                               const prep_t &t,
-                                                               const FoldConst &k) {
-        return (unsigned int)fold_fp64_from<PDOT>(f, p, t.y, k.nphi_d, k.n_phase) << SH;
-    }
-    template <bool PDOT, bool K0, int SH, bool RED>
-    __device__ __forceinline__ static unsigned int offset(double p, const prep_t &t,
-                                                          const FoldConst &k) {
-        return offset_from<PDOT, K0, SH, RED>(fpart(p, t), p, t, k);
-    }
-    __device__ __forceinline__ static bool has_pdot(double2 t) { return t.y != 0.0; }
-    __device__ __forceinline__ static bool k_zero(const prep_t &) { return true; }
-};
-template <> struct Fold<GCE_PHASE_SPLIT32> {
-    typedef float4 prep_t;
-    typedef float fpart_t;
-    static constexpr int kSlotBias = 0x4B400000;  // bits of 1.5 2^23
-    __device__ __forceinline__ static prep_t prepare(float4 t) { return t; }
-    template <bool PDOT>
-    __device__ __forceinline__ static int raw_slot(float4 p, const prep_t &t, const FoldConst &k) {
-        return fold_split<PDOT>(p, t, k.nphi_f, k.zoff) + kSlotBias;
-    }
-    __device__ __forceinline__ static fpart_t fpart(float4 p, const prep_t &t) {
-        return fold_split_fpart(p, t);
-    }
-    // RED: re-reduce the residual without Pdot as well (narrow slot range)
-    template <bool PDOT, bool K0, int SH, bool RED>
-    __device__ __forceinline__ static unsigned int offset_from(fpart_t f, float4 p,
-                                                               const prep_t &t,
-                                                               const FoldConst &k) {
-        return (unsigned int)(fold_split_from<PDOT, RED>(f, p, t, k.nphi_f, k.zoff) + kSlotBias)
-               << SH;
-    }
-    template <bool PDOT, bool K0, int SH, bool RED>
-    __device__ __forceinline__ static unsigned int offset(float4 p, const prep_t &t,
-                                                          const FoldConst &k) {
-        return offset_from<PDOT, K0, SH, RED>(fpart(p, t), p, t, k);
-    }
-    __device__ __forceinline__ static bool has_pdot(float4 t) {
-        return t.z != 0.0f || t.w != 0.0f;
-    }
-    __device__ __forceinline__ static bool k_zero(const prep_t &) { return true; }
-};
-template <> struct Fold<GCE_PHASE_FIXED32> {
-    typedef FixedPrep prep_t;
-    typedef unsigned int fpart_t;
-    static constexpr int kSlotBias = 0;
-    __device__ __forceinline__ static prep_t prepare(const FixedTrial &t) { return fixed_prep(t); }
-    template <bool PDOT>
-    __device__ __forceinline__ static int raw_slot(uint4 p, const prep_t &t, const FoldConst &k) {
-        return fold_fixed<PDOT>(p, t, (unsigned int)k.n_phase);
-    }
-    __device__ __forceinline__ static fpart_t fpart(uint4 p, const prep_t &t) {
-        return fold_fixed_fpart(p, t);
-    }
-    template <bool PDOT, bool K0, int SH, bool RED>
-    __device__ __forceinline__ static unsigned int offset_from(fpart_t f, uint4 p, const prep_t &t,
-                                                               const FoldConst &k) {
-        return fold_fixed_bin_from<PDOT, K0>(f, p, t, (unsigned int)k.n_phase) << SH;
-    }
-    template <bool PDOT, bool K0, int SH, bool RED>
-    __device__ __forceinline__ static unsigned int offset(uint4 p, const prep_t &t,
-                                                          const FoldConst &k) {
-        return offset_from<PDOT, K0, SH, RED>(fpart(p, t), p, t, k);
-    }
-    __device__ __forceinline__ static bool has_pdot(const FixedTrial &t) {
-        return (t.i.z | t.i.w) != 0u;
-    }
-    __device__ __forceinline__ static bool k_zero(const prep_t &t) { return t.k == 0u; }
-};
-
-// The increment carries no memory clobber, so the compiler may schedule the
-// next points' shared loads around it; compiler_fence() before and after each
-// hot loop keeps the counters' plain loads and stores on their side of it.
-__device__ __forceinline__ void red_shared_add(unsigned int addr, unsigned int inc) {
-    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(inc));
-}
-__device__ __forceinline__ void compiler_fence() { asm volatile("" ::: "memory"); }
-
-// The hot loop: every point of [ka, kb) (shared memory, broadcast) folded for
-// the thread's TPT trials and counted into the thread's private counters.
-// base[s]: shared-memory address of trial s's logical slot 0 minus the mode's
-// slot bias (mod 2^32); a slot's word is base + (raw << SH), SH = log2(4 block).
-// Each point counts once, in its fine phase bin, also with 50 %-overlapping
-// bins (their counts are sums of adjacent fine bins, formed in the epilogue).
-// SHARED: the thread's trials share their period (period-major tiles), so the
-// fold's period part is computed once per point for all of them.
-template <int MODE, int TPT, int SH, bool PDOT, bool K0, bool RED, bool SHARED>
-__device__ __forceinline__ void count_points(
-    const typename ModeTraits<MODE>::point_t *__restrict__ pts, int ka, int kb,
-    const typename Fold<MODE>::prep_t (&tc)[TPT], const unsigned int (&base)[TPT],
-    const FoldConst &fk, unsigned int inc) {
-#pragma unroll 8
-    for (int k = ka; k < kb; ++k) {
-        const typename ModeTraits<MODE>::point_t p = pts[k];
-        typename Fold<MODE>::fpart_t fp{};
-        if (SHARED) fp = Fold<MODE>::fpart(p, tc[0]);
-#pragma unroll
-        for (int s = 0; s < TPT; ++s) {
-            const unsigned int addr =
-                base[s] + (SHARED ? Fold<MODE>::template offset_from<PDOT, K0, SH, RED>(fp, p, tc[s], fk)
-                                  : Fold<MODE>::template offset<PDOT, K0, SH, RED>(p, tc[s], fk));
-#if defined(GCE_CHECK_SLOTS)
-            // checked builds: the logical slot of this increment must lie in the
-            // kept range; a miss is flagged and the access skipped
-            const int lslot =
-                (int)(addr - (base[s] + ((unsigned int)Fold<MODE>::kSlotBias << SH))) >> SH;
-            if (lslot < fk.zmin || lslot > fk.zmax) {
-                atomicOr(fk.err, (unsigned int)ERR_SLOT);
-                continue;
-            }
-#endif
-            red_shared_add(addr, inc);
-        }
-    }
-}
-
-template <int MODE, int TPT, int SH, bool PDOT, bool K0, bool RED = false>
-__device__ __forceinline__ void count_points_any(
-    bool shared, const typename ModeTraits<MODE>::point_t *__restrict__ pts, int ka, int kb,
-    const typename Fold<MODE>::prep_t (&tc)[TPT], const unsigned int (&base)[TPT],
-    const FoldConst &fk, unsigned int inc) {
-    constexpr bool SH_OK = PDOT && TPT > 1;  // sharing pays only with a Pdot term
-    if (SH_OK && shared) count_points<MODE, TPT, SH, PDOT, K0, RED, SH_OK>(pts, ka, kb, tc, base, fk, inc);
-    else count_points<MODE, TPT, SH, PDOT, K0, RED, false>(pts, ka, kb, tc, base, fk, inc);
-}
-
-// c_ij of one phase bin at the end of a magnitude segment (low - snapshot), with
-// the snapshot moved up to the current count: the new word is cur:cur (a byte
-// permute), and new - old = (cur - prev) << 16.
-__device__ __forceinline__ int take_segment(unsigned int *w) {
-    const unsigned int v = *w;
-    const unsigned int nv = __byte_perm(v, 0u, 0x1010);
-    *w = nv;
-    return (int)((nv - v) >> 16);
-}
-
-// Counter word formats.  Each (trial, slot) has one 32-bit shared word.
-//   FMT_SNAP: (snapshot << 16) | count, for curves of up to 65535 points.  The
-//     count is cumulative; the snapshot is the count at the end of the previous
-//     magnitude segment, so the segment's count is count - snapshot.
-//   FMT_PK2: (C << 20) | (B << 10) | A, for curves of at most kPk2MaxN points.
-//     Consecutive non-empty magnitude segments alternate between the fields A
-//     (increment 1) and B (increment 1 << 10); C is the cumulative count of the
-//     segments already swept.  One sweep then serves two segments: it reads A and
-//     B, adds them to C and clears them.  No field can overflow: each is at most
-//     the curve's point count.
-enum { FMT_SNAP = 0, FMT_PK2 = 1 };
-constexpr int kPk2MaxN = 1023;
-constexpr unsigned int kPk2IncB = 1u << 10;
-
-// Per counter word: the byte offsets 8 c into the c ln c table of the counts a
-// sweep reads, and the word it leaves behind.
-template <int FMT, bool SEG> struct Fields;
-template <> struct Fields<FMT_SNAP, true> {  // the segment's count; snapshot moved up
-    static constexpr int NF = 1;
-    __device__ __forceinline__ static unsigned int get(unsigned int v, unsigned int (&o)[1]) {
-        const unsigned int nv = __byte_perm(v, 0u, 0x1010);
-        o[0] = (nv - v) >> 13;
-        return nv;
-    }
-    // an extra slot's segment count joins its bin's first word
-    __device__ __forceinline__ static unsigned int merge(unsigned int first, unsigned int extra) {
-        return first + (extra & 0xffffu) - (extra >> 16);
-    }
-};
-template <> struct Fields<FMT_SNAP, false> {  // the cumulative count; word cleared
-    static constexpr int NF = 1;
-    __device__ __forceinline__ static unsigned int get(unsigned int v, unsigned int (&o)[1]) {
-        o[0] = (v & 0xffffu) << 3;
-        return 0u;
-    }
-};
-template <> struct Fields<FMT_PK2, true> {  // segments A and B; both added to C
-    static constexpr int NF = 2;
-    __device__ __forceinline__ static unsigned int get(unsigned int v, unsigned int (&o)[2]) {
-        o[0] = (v << 3) & 0x1ff8u;
-        o[1] = (v >> 7) & 0x1ff8u;
-        return (v & 0xfff00000u) + ((o[0] + o[1]) << 17);
-    }
-    __device__ __forceinline__ static unsigned int merge(unsigned int first, unsigned int extra) {
-        return first + extra;
-    }
-};
-template <> struct Fields<FMT_PK2, false> {  // C; word cleared
-    static constexpr int NF = 1;
-    __device__ __forceinline__ static unsigned int get(unsigned int v, unsigned int (&o)[1]) {
-        o[0] = (v >> 17) & 0x7ff8u;
-        return 0u;
-    }
-};
-
-// The entropy epilogue: for each of the thread's TPT trials, sum_j T(c_j) over
-// the n phase bins, T(c) = c ln c from the fixed-point table, for every count
-// the word format holds (one, or two segments for FMT_PK2 with SEG).  The
-// trial's counters for the window of logical slots [L, R] start at shared
-// address p0[s] (slot L), `stride` bytes apart; slot L + i counts bin
-// (L + i) mod n, so the first n slots hold one bin each and the
-// e = R - L + 1 - n extra slots L + n + i more points of the bin of slot
-// L + (i mod n) (SPLIT32's two slots per bin).
-// SEG: the counts since the last sweep.  Each extra word is first merged into
-// its bin's first word and cleared, so the sweep proper reads one word per bin;
-// after the last segment every extra word is therefore 0.
-// !SEG: the cumulative counts c_j of the first slots (the marginal term), each
-// word cleared after it is read, so the next work item starts from zero
-// counters without a separate pass.
-// OVL (50 %-overlapping bins, Sec. 2.3): overlapping bin j holds the fine bins j
-// and j + 1 (mod n), so the sum is over T(c_j + c_(j+1)): the first bin is
-// peeled off, each later bin pairs with the one before it, and the last pairs
-// with the first (table offsets add like the counts).  G bins of every trial
-// are loaded before any is stored, so the loads overlap.
-template <int TPT, int FMT, bool SEG, bool ALL_SMEM, bool OVL, int STRIDE>
-struct Sweep {
-    typedef Fields<FMT, SEG> F;
-    static constexpr int NF = F::NF;
-    unsigned int *const cnt;               // the thread's counter words
-    const unsigned long long *const s_tab;  // the c ln c table in shared memory
-    const int table_smem;
-    const unsigned long long *const g_tab;
-    unsigned int first[TPT][NF] = {}, prev[TPT][NF] = {};
-
-    // T(c) for the byte offset o = 8 c
-    __device__ __forceinline__ unsigned long long look(unsigned int o) const {
-        const unsigned long long *e = reinterpret_cast<const unsigned long long *>(
-            reinterpret_cast<const char *>(s_tab) + o);
-        if (ALL_SMEM) return *e;
-        const int c = (int)(o >> 3);
-        return c < table_smem ? *e : __ldg(g_tab + c);
-    }
-
-    // G bins of trial s at words cnt[w[s]], cnt[w[s] + STRIDE], ...; PEEL: the
-    // first bin of an OVL sweep
-    template <int G, bool PEEL>
-    __device__ __forceinline__ void step(int (&w)[TPT], unsigned long long (&acc)[TPT]) {
-        unsigned int v[TPT][G];
-#pragma unroll
-        for (int s = 0; s < TPT; ++s)
-#pragma unroll
-            for (int g = 0; g < G; ++g) v[s][g] = cnt[w[s] + g * STRIDE];
-        unsigned long long t[TPT];
-#pragma unroll
-        for (int s = 0; s < TPT; ++s) {
-            t[s] = 0ull;
-#pragma unroll
-            for (int g = 0; g < G; ++g) {
-                unsigned int o[NF];
-                v[s][g] = F::get(v[s][g], o);  // v now holds the word to store
-#pragma unroll
-                for (int f = 0; f < NF; ++f) {
-                    if (OVL) {
-                        if (PEEL && g == 0) first[s][f] = o[f];
-                        else t[s] += look(prev[s][f] + o[f]);
-                        prev[s][f] = o[f];
-                    } else {
-                        t[s] += look(o[f]);
-                    }
-                }
-            }
-        }
-#pragma unroll
-        for (int s = 0; s < TPT; ++s) {
-#pragma unroll
-            for (int g = 0; g < G; ++g) cnt[w[s] + g * STRIDE] = v[s][g];
-            acc[s] += t[s];
-            w[s] += G * STRIDE;
-        }
-    }
-
-    // w0[s]: word offset (from cnt) of trial s's first window slot; e: extra
-    // slots (SEG only)
-    __device__ __forceinline__ void run(const int (&w0)[TPT], int n, int e,
-                                        unsigned long long (&acc)[TPT]) {
-        if (SEG) {
-            for (int i = 0, b = 0; i < e; ++i, b = (b + 1 == n) ? 0 : b + 1) {
-#pragma unroll
-                for (int s = 0; s < TPT; ++s) {
-                    unsigned int *q = cnt + w0[s] + (n + i) * STRIDE;
-                    unsigned int *f = cnt + w0[s] + b * STRIDE;
-                    const unsigned int x = *q;
-                    *q = 0u;
-                    *f = merge(*f, x);
-                }
-            }
-        }
-        int w[TPT];
-#pragma unroll
-        for (int s = 0; s < TPT; ++s) w[s] = w0[s];
-        constexpr int G = TPT * NF >= 4 ? 2 : 4;
-        int j = 0;
-        if (OVL) {
-            step<1, true>(w, acc);
-            j = 1;
-        }
-        for (; j + G <= n; j += G) step<G, false>(w, acc);
-        if (G > 2 && (n - j) >= 2) {
-            step<2, false>(w, acc);
-            j += 2;
-        }
-        if (j < n) step<1, false>(w, acc);
-        if (OVL) {
-#pragma unroll
-            for (int s = 0; s < TPT; ++s)
-#pragma unroll
-                for (int f = 0; f < NF; ++f) acc[s] += look(prev[s][f] + first[s][f]);
-        }
-    }
-
-  private:
-    template <bool S = SEG>
-    __device__ __forceinline__ static unsigned int merge(unsigned int w, unsigned int x) {
-        if constexpr (S) return F::merge(w, x);
-        else return w;
-    }
-};
-
-// Dispatch of the sweeps of one work item over the run-time choices (overlapping
-// bins, whole table in shared memory).
-template <int TPT, int STRIDE>
-struct Sweeper {
-    unsigned int *cnt;
-    const unsigned long long *s_tab;
-    int table_smem;
-    const unsigned long long *g_tab;
-    int n;  // phase bins
-
-    template <int FMT>
-    __device__ __forceinline__ void segment(bool ovl, bool tab_all, const int (&w0)[TPT], int e,
-                                            unsigned long long (&acc)[TPT]) const {
-        if (ovl) {
-            if (tab_all) Sweep<TPT, FMT, true, true, true, STRIDE>{cnt, s_tab, table_smem, g_tab}.run(w0, n, e, acc);
-            else Sweep<TPT, FMT, true, false, true, STRIDE>{cnt, s_tab, table_smem, g_tab}.run(w0, n, e, acc);
-        } else {
-            if (tab_all) Sweep<TPT, FMT, true, true, false, STRIDE>{cnt, s_tab, table_smem, g_tab}.run(w0, n, e, acc);
-            else Sweep<TPT, FMT, true, false, false, STRIDE>{cnt, s_tab, table_smem, g_tab}.run(w0, n, e, acc);
-        }
-    }
-    template <int FMT>
-    __device__ __forceinline__ void marginal(bool ovl, bool tab_all, const int (&w0)[TPT],
-                                             unsigned long long (&acc)[TPT]) const {
-        if (ovl) {
-            if (tab_all) Sweep<TPT, FMT, false, true, true, STRIDE>{cnt, s_tab, table_smem, g_tab}.run(w0, n, 0, acc);
-            else Sweep<TPT, FMT, false, false, true, STRIDE>{cnt, s_tab, table_smem, g_tab}.run(w0, n, 0, acc);
-        } else {
-            if (tab_all) Sweep<TPT, FMT, false, true, false, STRIDE>{cnt, s_tab, table_smem, g_tab}.run(w0, n, 0, acc);
-            else Sweep<TPT, FMT, false, false, false, STRIDE>{cnt, s_tab, table_smem, g_tab}.run(w0, n, 0, acc);
-        }
-    }
-};
-
-// fh of a SPLIT32 trial (other modes: unused)
-__device__ __forceinline__ float split_fh(const float4 &t) { return t.x; }
-template <class T>
-__device__ __forceinline__ float split_fh(const T &) { return 0.0f; }
-
-
-// The slots a SPLIT32 fold can reach.  The fold's residual x obeys |x| <=
-// 1/2 + 2^-23 |th fh| (1 + 2^-22) + 2^-23 without the Pdot term (the two
-// cross terms are each below 2^-24 |th fh|, and three roundings), and |x| <=
-// 1/2 exactly with it (x is re-rounded); the slot is floor(x n + n), monotone
-// in x.  The bound is taken in FP32 with margins (a factor 1.01 and 2^-16)
-// far above its own rounding; cyc_max >= max |tau| f over the warp's trials.
-__device__ __forceinline__ void split_slot_window(bool pdot, float cyc_max, int n_phase, int &zlo,
-                                                  int &zhi) {
-    const float nf = (float)n_phase;
-    const float xm = 0.5f + (pdot ? 0.0f : cyc_max * 1.2040e-7f) + 1.5259e-5f;  // 1.01 2^-23, 2^-16
-    zlo = max((int)floorf(nf - nf * xm), 0);
-    zhi = min((int)floorf(nf + nf * xm), 2 * n_phase - 1);
-}
-
-// Chan et al.'s pairwise update of (count, mean, M2) moments.
-__device__ __forceinline__ void chan_merge(double &n, double &mean, double &m2, double nb,
-                                           double meanb, double m2b) {
-    if (nb <= 0.0) return;
-    if (n <= 0.0) {
-        n = nb;
-        mean = meanb;
-        m2 = m2b;
-        return;
-    }
-    const double tot = n + nb;
-    const double d = meanb - mean;
-    mean += d * (nb / tot);
-    m2 += m2b + d * d * (n * nb / tot);
-    n = tot;
-}
-
-// CTAs per SM the register allocation is sized for.  With two trials per
-// thread the counters (and FP64's wider staged points) already limit shared
-// memory to about three 256-thread CTAs per SM at 15 phase bins, so those
-// kernels take the registers that frees (80 at 256 threads) instead of 64.
-// Four trials per thread need four times the counters of one: at most 512
-// threads per SM fit, and those kernels take up to 128 registers.  One trial
-// per thread is the shape for many phase bins (50 and up), where the counters
-// again leave room for about 512 threads per SM: 128 registers as well.
-constexpr int main_min_blocks(int tpt, int log2b) {
-    return tpt == 2 ? (log2b >= 9 ? 2 : (log2b == 8 ? 3 : (log2b == 7 ? 6 : 8)))
-                    : (log2b >= 9 ? 1 : (log2b == 8 ? 2 : (log2b == 7 ? 4 : 8)));
-}
-
-template <int MODE, int TPT, int LOG2B>
-__global__ void __launch_bounds__(1 << LOG2B, main_min_blocks(TPT, LOG2B)) k_main(MainArgs a) {
-    typedef typename ModeTraits<MODE>::point_t point_t;
-    typedef typename ModeTraits<MODE>::trial_t trial_t;
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ long long s_item;
-
-    if (a.state->err) return;  // inputs failed the device checks: no work
-
-    constexpr int B = 1 << LOG2B;
-    constexpr int SH = LOG2B + 2;  // log2 of the byte stride between a thread's slots
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int n_phase = a.n_phase, n_mag = a.n_mag;
-    constexpr bool SPLIT = MODE == GCE_PHASE_SPLIT32;
-    const int ovl = a.overlap ? 1 : 0;
-    const bool narrow = SPLIT && a.narrow != 0;
-    const SlotRange zr = slot_range(MODE, n_phase, narrow);
-    const int n_slots = slots_per_trial(MODE, n_phase, narrow);
-    const int slot_off = -zr.zmin;  // physical index of logical slot l: l + slot_off
-    const int stride_j = B, stride_s = n_slots * B;
-
-    // the table first (its address is then a constant), padded to an even count
-    // so that the staged points after it stay 16-byte aligned
-    unsigned long long *s_tab = reinterpret_cast<unsigned long long *>(smem);
-    point_t *s_pts = reinterpret_cast<point_t *>(s_tab + ((a.table_smem + 1) & ~1));
-    unsigned int *s_cnt = reinterpret_cast<unsigned int *>(s_pts + a.chunk);
-    int *s_seg = reinterpret_cast<int *>(s_cnt + TPT * n_slots * B);
-    unsigned long long *s_top =
-        reinterpret_cast<unsigned long long *>(s_seg + ((n_mag + 2) & ~1));
-    double *s_stat = reinterpret_cast<double *>(s_top + (B / 32) * (a.k > 0 ? a.k : 1));
-
-    for (int i = tid; i < a.table_smem; i += B) s_tab[i] = a.table[i];
-
-    const point_t *g_pts = reinterpret_cast<const point_t *>(a.payload);
-    const trial_t *g_tr = reinterpret_cast<const trial_t *>(a.trialc);
-    unsigned int *my_cnt = s_cnt + tid;
-    // counters start at zero; every work item's final sweep clears the words it
-    // used, so later items start from zero as well
-    for (int i = 0; i < TPT * n_slots; ++i) my_cnt[i * B] = 0u;
-#if defined(GCE_CHECK_SLOTS)
-    FoldConst fk = fold_const(n_phase);
-    fk.zmin = zr.zmin;
-    fk.zmax = zr.zmax;
-    fk.err = &a.state->err;
-#else
-    const FoldConst fk = fold_const(n_phase);
-#endif
-    unsigned int base[TPT];
-    unsigned int *wbase[TPT];  // physical slot 0 of trial s
-#pragma unroll
-    for (int s = 0; s < TPT; ++s) {
-        wbase[s] = my_cnt + s * stride_s;
-        base[s] = (unsigned int)__cvta_generic_to_shared(wbase[s]) + ((unsigned int)slot_off << SH) -
-                  ((unsigned int)Fold<MODE>::kSlotBias << SH);
-    }
-    // max |tau| of the job (SPLIT32 slot windows), rounded up to FP32
-    const float tau_max_f =
-        SPLIT ? __double2float_ru(__longlong_as_double((long long)a.state->tau_max_bits)) : 0.0f;
-
-    int staged_curve = -1, staged_lo = -1;
-    // the tile whose trial constants, flags and counter window are loaded: work
-    // items of the same tile reuse them
-    int cur_tile = -1;
-    typename Fold<MODE>::prep_t tc[TPT];
-    long long tt[TPT];
-    bool pdot = false, k0 = true;
-    const bool pdm = a.pd_major != 0;
-    int wl[TPT];           // word offset (from my_cnt) of each trial's first window slot
-
-    int n_extra = 0;       // window slots beyond n_phase
-    long long item = 0, item_end = 0;
-    for (;;) {
-        if (item >= item_end) {
-            __syncthreads();
-            if (tid == 0) s_item = (long long)atomicAdd(&a.state->work, (unsigned long long)a.grab);
-            __syncthreads();
-            item = s_item;
-            item_end = min(item + (long long)a.grab, a.n_items);
-            if (item >= a.n_items) break;
-        }
-        // items [0, n_long_items) run curve-major over the long curves (consecutive
-        // items share the staged curve); the rest tile-major over the short curves
-        // at the end of the order (consecutive items share the tile's trials)
-        int ci, tile;
-        if (item < a.n_long_items) {
-            ci = (int)(item / a.n_tiles);
-            tile = (int)(item - (long long)ci * a.n_tiles);
-        } else {
-            const long long j = item - a.n_long_items;
-            tile = (int)(j / a.n_short);
-            ci = a.n_long + (int)(j - (long long)tile * a.n_short);
-        }
-        const int c = a.order[ci];
-        const long long off = a.offsets[c];
-        const int n = (int)(a.offsets[c + 1] - off);
-        const bool tab_all = n < a.table_smem;  // every count of this curve is <= n
-        if (c != staged_curve) {
-            __syncthreads();
-            for (int i = tid; i <= n_mag; i += B) s_seg[i] = a.seg[(long long)c * (n_mag + 1) + i];
-            staged_curve = c;
-            staged_lo = -1;
-        }
-
-        if (tile != cur_tile) {
-            cur_tile = tile;
-            bool any_pdot = false, all_k0 = true;
-            // trial indices (n_trials marks a slot past the grid): a run of B x TPT
-            // flat indices, or B periods x TPT Pdot values (period-major tiles)
-            long long p_idx = 0;
-            int q_base = 0;
-            if (pdm) {
-                p_idx = (long long)(tile % a.n_ptiles) * B + tid;
-                q_base = (tile / a.n_ptiles) * TPT;
-            }
-#pragma unroll
-            for (int s = 0; s < TPT; ++s) {
-                if (pdm)
-                    tt[s] = (p_idx < a.n_periods && q_base + s < a.n_pdots)
-                                ? (long long)(q_base + s) * a.n_periods + p_idx
-                                : a.n_trials;
-                else
-                    tt[s] = (long long)tile * (B * TPT) + (long long)s * B + tid;
-                trial_t tr{};
-                if (tt[s] < a.n_trials) {
-                    tr = g_tr[tt[s]];
-                    any_pdot |= Fold<MODE>::has_pdot(tr);
-                }
-                tc[s] = Fold<MODE>::prepare(tr);
-                all_k0 &= Fold<MODE>::k_zero(tc[s]);
-            }
-            pdot = __syncthreads_or(any_pdot) != 0;
-            k0 = MODE != GCE_PHASE_FIXED32 || __syncthreads_and(all_k0) != 0;
-            // live logical slots [L, R] of this warp's counters (warp-uniform)
-            int L = 0, R = n_phase - 1;
-            if (SPLIT) {
-                float fm = 0.0f;
-#pragma unroll
-                for (int s = 0; s < TPT; ++s)
-                    if (tt[s] < a.n_trials) fm = fmaxf(fm, fabsf(split_fh(tc[s])));
-                fm = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(fm)));
-                int zlo, zhi;
-                split_slot_window(pdot || narrow, tau_max_f * fm, n_phase, zlo, zhi);
-                L = max(zlo, zr.zmin);
-                R = min(zhi, zr.zmax);
-            }
-#pragma unroll
-            for (int s = 0; s < TPT; ++s) wl[s] = s * stride_s + (L + slot_off) * stride_j;
-            n_extra = R - L + 1 - n_phase;
-
-#if defined(GCE_CHECK_SLOTS)
-            // checked builds: every increment must also lie in the warp's window
-            fk.zmin = L;
-            fk.zmax = R;
-#endif
-        }
-
-        unsigned long long s_ij[TPT];
-#pragma unroll
-        for (int s = 0; s < TPT; ++s) s_ij[s] = 0ull;
-
-        // FMT_PK2 (one sweep per two non-empty segments) with 50 %-overlapping
-        // bins on curves of at most kPk2MaxN points, else FMT_SNAP (one sweep per
-        // segment).  Each count costs the same table lookup and 64-bit add in both
-        // formats; FMT_PK2 saves the loads, stores and the overlapping pairs' set-up
-        // of every other sweep, which pays with overlapping bins and costs more
-        // field arithmetic than it saves without them.
-        const bool pk2 = ovl && n <= kPk2MaxN;
-        const Sweeper<TPT, B> sw{my_cnt, s_tab, a.table_smem, a.table, n_phase};
-        int ended = 0;  // non-empty segments ended so far (FMT_PK2: field = ended & 1)
-        for (int lo = 0; lo < n; lo += a.chunk) {
-            const int hi = min(n, lo + a.chunk);
-            if (staged_lo != lo) {
-                __syncthreads();
-                const point_t *src = g_pts + off + lo;
-                for (int k = tid; k < hi - lo; k += B) s_pts[k] = src[k];
-                __syncthreads();
-                staged_lo = lo;
-            }
-            for (int i = 0; i < n_mag; ++i) {
-                const int s0 = s_seg[i], s1 = s_seg[i + 1];
-                const int ka = max(s0, lo), kb = min(s1, hi);
-                if (ka < kb) {
-                    const unsigned int inc = (pk2 && (ended & 1)) ? kPk2IncB : 1u;
-                    compiler_fence();
-                    const typename ModeTraits<MODE>::point_t *pp = s_pts;
-                    if (k0) {
-                        if (pdot) count_points_any<MODE, TPT, SH, true, true>(pdm, pp, ka - lo, kb - lo, tc, base, fk, inc);
-                        else if (SPLIT && narrow) count_points_any<MODE, TPT, SH, false, true, SPLIT>(pdm, pp, ka - lo, kb - lo, tc, base, fk, inc);
-                        else count_points_any<MODE, TPT, SH, false, true>(pdm, pp, ka - lo, kb - lo, tc, base, fk, inc);
-                    } else if (MODE == GCE_PHASE_FIXED32) {
-                        if (pdot) count_points_any<MODE, TPT, SH, true, false>(pdm, pp, ka - lo, kb - lo, tc, base, fk, inc);
-                        else count_points_any<MODE, TPT, SH, false, false>(pdm, pp, ka - lo, kb - lo, tc, base, fk, inc);
-                    }
-                    compiler_fence();
-                }
-                if (s1 > s0 && s1 > lo && s1 <= hi) {
-                    // end of non-empty magnitude segment i: sweep its counts (FMT_PK2:
-                    // after every second one)
-                    if (!pk2) sw.segment<FMT_SNAP>(ovl, tab_all, wl, n_extra, s_ij);
-                    else if (ended & 1) sw.segment<FMT_PK2>(ovl, tab_all, wl, n_extra, s_ij);
-                    ++ended;
-                }
-            }
-        }
-        if (pk2 && (ended & 1)) sw.segment<FMT_PK2>(ovl, tab_all, wl, n_extra, s_ij);  // the last, alone
-
-        // sum_j c_j ln c_j from the cumulative counters, then H (the counts total
-        // 2N with overlapping bins, every point being in two bins); this sweep
-        // clears the counters for the next item (the extra slots are already 0)
-        const double inv = kTabInvScale / (double)(n * (1 + ovl));
-        unsigned long long key[TPT], sjs[TPT];
-        float hv[TPT];
-#pragma unroll
-        for (int s = 0; s < TPT; ++s) sjs[s] = 0ull;
-        if (pk2) sw.marginal<FMT_PK2>(ovl, tab_all, wl, sjs);
-        else sw.marginal<FMT_SNAP>(ovl, tab_all, wl, sjs);
-#pragma unroll
-        for (int s = 0; s < TPT; ++s) {
-            const unsigned long long sj = sjs[s];
-            long long d = (long long)(sj - s_ij[s]);
-            if (d < 0) d = 0;
-            const float h = __double2float_rn(__dmul_rn(__ll2double_rn(d), inv));
-            hv[s] = h;
-            key[s] = kNoKey;
-            if (tt[s] < a.n_trials) {
-                if (a.out) a.out[(long long)c * a.n_trials + tt[s]] = h;
-                key[s] = ((unsigned long long)__float_as_uint(h) << 32) | (unsigned long long)tt[s];
-            }
-        }
-
-        if (a.stats) {
-            // moments of the tile's H for the significance of Eq. 5: per warp, sums of
-            // H - shift in FP32 (shift = lane 0's first value, so the sums stay small),
-            // then (count, mean, M2) in FP64, merged over the warps in order
-            const float shift = __shfl_sync(0xffffffffu, hv[0], 0);
-            float s1 = 0.f, s2 = 0.f, cnt = 0.f;
-#pragma unroll
-            for (int s = 0; s < TPT; ++s)
-                if (tt[s] < a.n_trials) {
-                    const float dd = hv[s] - shift;
-                    s1 += dd;
-                    s2 = __fmaf_rn(dd, dd, s2);
-                    cnt += 1.f;
-                }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-                s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-                cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-            }
-            if (lane == 0) {
-                const double nw = cnt;
-                const double mu = nw > 0 ? (double)shift + (double)s1 / nw : 0.0;
-                const double m2 = nw > 0 ? fmax((double)s2 - (double)s1 * (double)s1 / nw, 0.0) : 0.0;
-                s_stat[3 * warp] = nw;
-                s_stat[3 * warp + 1] = mu;
-                s_stat[3 * warp + 2] = m2;
-            }
-            __syncthreads();
-            if (tid == 0) {
-                double nn = 0.0, mu = 0.0, m2 = 0.0;
-                for (int w = 0; w < (B >> 5); ++w)
-                    chan_merge(nn, mu, m2, s_stat[3 * w], s_stat[3 * w + 1], s_stat[3 * w + 2]);
-                TileStats *t = a.stats + (long long)c * a.n_tiles + tile;
-                t->n = nn;
-                t->mean = mu;
-                t->m2 = m2;
-            }
-        }
-
-        if (a.cand) {
-            // tile top-k: k rounds of warp minima, then one warp merges the warps' lists
-            const int nw = B >> 5;
-            for (int r = 0; r < a.k; ++r) {
-                unsigned long long mine = key[0];
-#pragma unroll
-                for (int s = 1; s < TPT; ++s) mine = key[s] < mine ? key[s] : mine;
-                const unsigned long long m = warp_min_key(mine);
-                if (lane == 0) s_top[warp * a.k + r] = m;
-#pragma unroll
-                for (int s = 0; s < TPT; ++s)
-                    if (key[s] == m) key[s] = kNoKey;
-            }
-            __syncthreads();
-            if (warp == 0) {
-                unsigned long long *dst = a.cand + ((long long)c * a.n_tiles + tile) * a.k;
-                const int tot = nw * a.k;
-                for (int r = 0; r < a.k; ++r) {
-                    unsigned long long mine = kNoKey;
-                    for (int i = lane; i < tot; i += 32) mine = s_top[i] < mine ? s_top[i] : mine;
-                    const unsigned long long m = warp_min_key(mine);
-                    for (int i = lane; i < tot; i += 32)
-                        if (s_top[i] == m) s_top[i] = kNoKey;
-                    __syncwarp();
-                    if (lane == 0) dst[r] = m;
-                }
-            }
-        }
-        ++item;
-    }
-}
 
 // Per-curve merge of the tiles' candidates: k rounds of "smallest key above the
 // previous one" (keys are unique: H bits in the high word, trial index low).
@@ -919,71 +138,29 @@ __global__ void k_counts(MainArgs a, long long n_cells, const long long *cell_cu
     }
 }
 
-template <int MODE, int TPT, int LOG2B>
-cudaError_t launch_main_t(int grid, size_t smem, const MainArgs &a, cudaStream_t s) {
-    k_main<MODE, TPT, LOG2B><<<grid, 1 << LOG2B, smem, s>>>(a);
-    return cudaGetLastError();
-}
-
-// The kernel instantiations: mode x trials per thread x block size.
-template <int MODE, int TPT>
-const void *kernel_for_block(int block) {
-    switch (block) {
-        case 64: return (const void *)k_main<MODE, TPT, 6>;
-        case 128: return (const void *)k_main<MODE, TPT, 7>;
-        case 256: return (const void *)k_main<MODE, TPT, 8>;
-        case 512: return (const void *)k_main<MODE, TPT, 9>;
-        default: return nullptr;
-    }
-}
-
-template <int MODE, int TPT>
-cudaError_t launch_for_block(int block, int grid, size_t smem, const MainArgs &a, cudaStream_t s) {
-    switch (block) {
-        case 64: return launch_main_t<MODE, TPT, 6>(grid, smem, a, s);
-        case 128: return launch_main_t<MODE, TPT, 7>(grid, smem, a, s);
-        case 256: return launch_main_t<MODE, TPT, 8>(grid, smem, a, s);
-        case 512: return launch_main_t<MODE, TPT, 9>(grid, smem, a, s);
-        default: return cudaErrorInvalidValue;
-    }
-}
-
 }  // namespace
 
 size_t main_smem_bytes(int mode, int block, int tpt, int chunk, int n_phase, int n_mag,
-                       int table_smem, int k, int narrow) {
-    size_t pt = mode == GCE_PHASE_FP64 ? 8 : 16;
-    size_t b = 8 * (size_t)((table_smem + 1) & ~1) + pt * (size_t)chunk +
-               4 * (size_t)tpt * slots_per_trial(mode, n_phase, narrow != 0) * block +
-               4 * (size_t)((n_mag + 2) & ~1) + 8 * (size_t)(block / 32) * (size_t)(k > 0 ? k : 1) +
-               24 * (size_t)(block / 32);
-    return b;
+                       int table_smem, int k, int narrow, int half) {
+    return main_smem_layout(mode, block, tpt, chunk, n_phase, n_mag, table_smem, k, narrow, half)
+        .total;
 }
 
 size_t single_smem_bytes(int n_phase, int block) { return 4 * (size_t)n_phase * block; }
 
-const void *main_kernel_ptr(int mode, int tpt, int block) {
-    switch (mode * 8 + tpt) {
-        case GCE_PHASE_FP64 * 8 + 1: return kernel_for_block<GCE_PHASE_FP64, 1>(block);
-        case GCE_PHASE_FP64 * 8 + 2: return kernel_for_block<GCE_PHASE_FP64, 2>(block);
-        case GCE_PHASE_SPLIT32 * 8 + 1: return kernel_for_block<GCE_PHASE_SPLIT32, 1>(block);
-        case GCE_PHASE_SPLIT32 * 8 + 2: return kernel_for_block<GCE_PHASE_SPLIT32, 2>(block);
-        case GCE_PHASE_SPLIT32 * 8 + 4: return kernel_for_block<GCE_PHASE_SPLIT32, 4>(block);
-        case GCE_PHASE_FIXED32 * 8 + 1: return kernel_for_block<GCE_PHASE_FIXED32, 1>(block);
-        case GCE_PHASE_FIXED32 * 8 + 2: return kernel_for_block<GCE_PHASE_FIXED32, 2>(block);
-        case GCE_PHASE_FIXED32 * 8 + 4: return kernel_for_block<GCE_PHASE_FIXED32, 4>(block);
+const void *main_kernel_ptr(int mode, int tpt, int block, bool ovl) {
+    switch (mode) {
+        case GCE_PHASE_FP64: return main_kernel_ptr_fp64(tpt, block, ovl);
+        case GCE_PHASE_SPLIT32: return main_kernel_ptr_split32(tpt, block, ovl);
+        case GCE_PHASE_FIXED32: return main_kernel_ptr_fixed32(tpt, block, ovl);
         default: return nullptr;
     }
 }
 
-// The kernel's dynamic shared-memory limit is raised to the device's opt-in
-// maximum, never set to one job's size, so that calls planned on other host
-// threads (which all set the same value) cannot lower it between their planning
-// and their launch.
 // The dynamic shared memory a CTA of the kernel can have: the device's opt-in
 // maximum less the kernel's static shared memory (0 if the kernel is unknown).
-size_t main_dynamic_smem_limit(int mode, int tpt, int block, size_t smem_optin) {
-    const void *f = main_kernel_ptr(mode, tpt, block);
+size_t main_dynamic_smem_limit(int mode, int tpt, int block, bool ovl, size_t smem_optin) {
+    const void *f = main_kernel_ptr(mode, tpt, block, ovl);
     cudaFuncAttributes fa;
     if (!f || cudaFuncGetAttributes(&fa, f) != cudaSuccess || fa.sharedSizeBytes > smem_optin) {
         cudaGetLastError();
@@ -992,25 +169,23 @@ size_t main_dynamic_smem_limit(int mode, int tpt, int block, size_t smem_optin) 
     return smem_optin - fa.sharedSizeBytes;
 }
 
-cudaError_t main_kernel_attrs(int mode, int tpt, int block, size_t smem_optin) {
-    const void *f = main_kernel_ptr(mode, tpt, block);
+// The kernel's dynamic shared-memory limit is raised to that maximum, never set
+// to one job's size, so that calls planned on other host threads (which all set
+// the same value) cannot lower it between their planning and their launch.
+cudaError_t main_kernel_attrs(int mode, int tpt, int block, bool ovl, size_t smem_optin) {
+    const void *f = main_kernel_ptr(mode, tpt, block, ovl);
     if (!f) return cudaErrorInvalidValue;
-    const size_t lim = main_dynamic_smem_limit(mode, tpt, block, smem_optin);
+    const size_t lim = main_dynamic_smem_limit(mode, tpt, block, ovl, smem_optin);
     if (lim == 0) return cudaErrorInvalidValue;
     return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim);
 }
 
 cudaError_t launch_main(int mode, int tpt, int block, int grid, size_t smem, const MainArgs &a,
                         cudaStream_t s) {
-    switch (mode * 8 + tpt) {
-        case GCE_PHASE_FP64 * 8 + 1: return launch_for_block<GCE_PHASE_FP64, 1>(block, grid, smem, a, s);
-        case GCE_PHASE_FP64 * 8 + 2: return launch_for_block<GCE_PHASE_FP64, 2>(block, grid, smem, a, s);
-        case GCE_PHASE_SPLIT32 * 8 + 1: return launch_for_block<GCE_PHASE_SPLIT32, 1>(block, grid, smem, a, s);
-        case GCE_PHASE_SPLIT32 * 8 + 2: return launch_for_block<GCE_PHASE_SPLIT32, 2>(block, grid, smem, a, s);
-        case GCE_PHASE_SPLIT32 * 8 + 4: return launch_for_block<GCE_PHASE_SPLIT32, 4>(block, grid, smem, a, s);
-        case GCE_PHASE_FIXED32 * 8 + 1: return launch_for_block<GCE_PHASE_FIXED32, 1>(block, grid, smem, a, s);
-        case GCE_PHASE_FIXED32 * 8 + 2: return launch_for_block<GCE_PHASE_FIXED32, 2>(block, grid, smem, a, s);
-        case GCE_PHASE_FIXED32 * 8 + 4: return launch_for_block<GCE_PHASE_FIXED32, 4>(block, grid, smem, a, s);
+    switch (mode) {
+        case GCE_PHASE_FP64: return launch_main_fp64(tpt, block, grid, smem, a, s);
+        case GCE_PHASE_SPLIT32: return launch_main_split32(tpt, block, grid, smem, a, s);
+        case GCE_PHASE_FIXED32: return launch_main_fixed32(tpt, block, grid, smem, a, s);
         default: return cudaErrorInvalidValue;
     }
 }

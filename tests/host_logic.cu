@@ -1,6 +1,6 @@
 // Host-side planning logic of the CE library, checked on the CPU: the header
-// functions that size the trial tiles, the first level of the top-k merge and
-// the SPLIT32 counter slots.  Built by tests/test_host_logic.py with nvcc and run
+// functions that size the trial tiles, the first level of the top-k merge, the
+// SPLIT32 counter slots and the CE kernel's shared-memory layout.  Built by tests/test_host_logic.py with nvcc and run
 // without a GPU: no CUDA runtime call is made.  Prints "ok" and returns 0, or
 // prints each failed check and returns 1.
 #include <cmath>
@@ -102,11 +102,41 @@ static void check_slot_range() {
     }
 }
 
+// The CE kernel's shared-memory layout (one function for the host's launch size
+// and the kernel's carve-up): regions in order, each aligned for its type (16
+// bytes for the staged points and the counters after them, 8 for the keys and
+// moments), the staged points sized 8 or 16 bytes each, and the total the sum
+// of the parts.
+static void check_smem_layout(std::mt19937_64 &rng) {
+    const int blocks[] = {64, 128, 256, 512};
+    const int tpts[] = {1, 2, 4};
+    for (int it = 0; it < 20000; ++it) {
+        const int mode = (int)(rng() % 3), B = blocks[rng() % 4], T = tpts[rng() % 3];
+        const int chunk = 32 * (1 + (int)(rng() % 256));
+        const int n_phase = 1 + (int)(rng() % GCE_MAX_PHASE_BINS);
+        const int n_mag = 1 + (int)(rng() % GCE_MAX_MAG_BINS);
+        const int table = 1 + (int)(rng() % 2048), k = (int)(rng() % (GCE_MAX_TOPK + 1));
+        const int narrow = (int)(rng() % 2), half = (int)(rng() % 2);
+        const MainSmemLayout L =
+            main_smem_layout(mode, B, T, chunk, n_phase, n_mag, table, k, narrow, half);
+        const unsigned int pt = (mode == GCE_PHASE_FP64 || half) ? 8u : 16u;
+        const unsigned int cnt = 4u * (unsigned int)(T * slots_per_trial(mode, n_phase, narrow != 0) * B);
+        CHECK(L.pts >= 8u * (unsigned int)table && L.pts % 16 == 0, "pts %u table %d", L.pts, table);
+        CHECK(L.cnt == L.pts + pt * (unsigned int)chunk && L.cnt % 16 == 0, "cnt %u", L.cnt);
+        CHECK(L.seg == L.cnt + cnt, "seg %u", L.seg);
+        CHECK(L.top >= L.seg + 4u * (unsigned int)(n_mag + 1) && L.top % 8 == 0, "top %u", L.top);
+        CHECK(L.stat == L.top + 8u * (unsigned int)((B / 32) * (k > 0 ? k : 1)) && L.stat % 8 == 0,
+              "stat %u", L.stat);
+        CHECK(L.total == L.stat + 24u * (unsigned int)(B / 32), "total %u", L.total);
+    }
+}
+
 int main() {
     std::mt19937_64 rng(20200611);
     check_tile_grid(rng);
     check_topk_groups(rng);
     check_slot_range();
+    check_smem_layout(rng);
     if (g_fail) {
         std::printf("%d checks failed\n", g_fail);
         return 1;
