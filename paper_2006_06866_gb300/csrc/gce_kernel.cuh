@@ -186,7 +186,10 @@ __device__ __forceinline__ void count_points(
     const FoldConst &fk, unsigned int inc) {
     typedef ModeTraits<MODE> MT;
     static_assert(!(HALF && PDOT), "half points carry no tau^2");
-#pragma unroll 8
+    // points unrolled by 16 (8 with the longer Pdot fold): measured faster than 8
+    // and 4 on every workload without a Pdot axis, and than 16 with one
+    constexpr int UNROLL = PDOT ? 8 : 16;
+#pragma unroll UNROLL
     for (int k = ka; k < kb; ++k) {
         const typename MT::point_t p =
             HALF ? MT::widen(static_cast<const typename MT::half_t *>(pts)[k])
@@ -249,11 +252,22 @@ constexpr unsigned int kPk2IncB = 1u << 10;
 
 // Per counter word: the byte offsets 8 c into the c ln c table of the counts a
 // sweep reads, and the word it leaves behind.
-template <int FMT, bool SEG> struct Fields;
-template <> struct Fields<FMT_SNAP, true> {  // the segment's count; snapshot moved up
+// What a sweep reads from each counter word.
+enum { SW_SEG = 0, SW_LAST = 1 };
+//   SW_SEG:  the counts of the segments since the last sweep (subtracted: the
+//            Sigma_ij T(c_ij) term), the word left with them moved to the
+//            cumulative part;
+//   SW_LAST: after the curve's last segment, those counts and the cumulative
+//            count c_j (added: the Sigma_j T(c_j) term), the word cleared.
+// Fields<FMT, KIND>::get returns the byte offsets 8 c into the c ln c table of
+// the NF counts, and the word to store back; sign(f) says whether count f is
+// added (+1) or subtracted (-1).
+template <int FMT, int KIND> struct Fields;
+template <> struct Fields<FMT_SNAP, SW_SEG> {
     static constexpr int NF = 1;
+    __device__ __forceinline__ static int sign(int) { return -1; }
     __device__ __forceinline__ static unsigned int get(unsigned int v, unsigned int (&o)[1]) {
-        const unsigned int nv = __byte_perm(v, 0u, 0x1010);
+        const unsigned int nv = __byte_perm(v, 0u, 0x1010);  // snapshot moved up
         o[0] = (nv - v) >> 13;
         return nv;
     }
@@ -262,15 +276,21 @@ template <> struct Fields<FMT_SNAP, true> {  // the segment's count; snapshot mo
         return first + (extra & 0xffffu) - (extra >> 16);
     }
 };
-template <> struct Fields<FMT_SNAP, false> {  // the cumulative count; word cleared
-    static constexpr int NF = 1;
-    __device__ __forceinline__ static unsigned int get(unsigned int v, unsigned int (&o)[1]) {
-        o[0] = (v & 0xffffu) << 3;
+template <> struct Fields<FMT_SNAP, SW_LAST> {
+    static constexpr int NF = 2;
+    __device__ __forceinline__ static int sign(int f) { return f == 0 ? -1 : 1; }
+    __device__ __forceinline__ static unsigned int get(unsigned int v, unsigned int (&o)[2]) {
+        o[0] = (__byte_perm(v, 0u, 0x1010) - v) >> 13;
+        o[1] = (v & 0xffffu) << 3;
         return 0u;
     }
+    __device__ __forceinline__ static unsigned int merge(unsigned int first, unsigned int extra) {
+        return Fields<FMT_SNAP, SW_SEG>::merge(first, extra);
+    }
 };
-template <> struct Fields<FMT_PK2, true> {  // segments A and B; both added to C
+template <> struct Fields<FMT_PK2, SW_SEG> {  // segments A and B; both added to C
     static constexpr int NF = 2;
+    __device__ __forceinline__ static int sign(int) { return -1; }
     __device__ __forceinline__ static unsigned int get(unsigned int v, unsigned int (&o)[2]) {
         o[0] = (v << 3) & 0x1ff8u;
         o[1] = (v >> 7) & 0x1ff8u;
@@ -280,36 +300,39 @@ template <> struct Fields<FMT_PK2, true> {  // segments A and B; both added to C
         return first + extra;
     }
 };
-template <> struct Fields<FMT_PK2, false> {  // C; word cleared
-    static constexpr int NF = 1;
-    __device__ __forceinline__ static unsigned int get(unsigned int v, unsigned int (&o)[1]) {
-        o[0] = (v >> 17) & 0x7ff8u;
+template <> struct Fields<FMT_PK2, SW_LAST> {  // A, B and C + A + B; word cleared
+    static constexpr int NF = 3;
+    __device__ __forceinline__ static int sign(int f) { return f == 2 ? 1 : -1; }
+    __device__ __forceinline__ static unsigned int get(unsigned int v, unsigned int (&o)[3]) {
+        o[0] = (v << 3) & 0x1ff8u;
+        o[1] = (v >> 7) & 0x1ff8u;
+        o[2] = ((v >> 17) & 0x7ff8u) + o[0] + o[1];
         return 0u;
+    }
+    __device__ __forceinline__ static unsigned int merge(unsigned int first, unsigned int extra) {
+        return first + extra;
     }
 };
 
-// The entropy epilogue: for each of the thread's TPT trials, sum_j T(c_j) over
-// the n phase bins, T(c) = c ln c from the fixed-point table, for every count
-// the word format holds (one, or two segments for FMT_PK2 with SEG).  The
-// trial's counters for the window of logical slots [L, R] start at shared
-// address p0[s] (slot L), `stride` bytes apart; slot L + i counts bin
-// (L + i) mod n, so the first n slots hold one bin each and the
-// e = R - L + 1 - n extra slots L + n + i more points of the bin of slot
-// L + (i mod n) (SPLIT32's two slots per bin).
-// SEG: the counts since the last sweep.  Each extra word is first merged into
-// its bin's first word and cleared, so the sweep proper reads one word per bin;
-// after the last segment every extra word is therefore 0.
-// !SEG: the cumulative counts c_j of the first slots (the marginal term), each
-// word cleared after it is read, so the next work item starts from zero
-// counters without a separate pass.
+// The entropy sweep: for each of the thread's TPT trials, the c ln c terms,
+// T(c) = c ln c from the fixed-point table, of every count the word format and
+// the sweep kind hold, added to or subtracted from acc (N H 2^32, Eq. 4 as
+// Sigma_j T(c_j) - Sigma_ij T(c_ij)).  The trial's counters for the window of
+// logical slots [L, R] start at word w0[s] (slot L), STRIDE words apart; slot
+// L + i counts bin (L + i) mod n, so the first n slots hold one bin each and
+// the e = R - L + 1 - n extra slots L + n + i more points of the bin of slot
+// L + (i mod n) (SPLIT32's two slots per bin).  Each extra word is first merged
+// into its bin's first word and cleared, so the sweep proper reads one word per
+// bin.  SW_LAST clears every word it reads, so the next work item starts from
+// zero counters without a separate pass.
 // OVL (50 %-overlapping bins, Sec. 2.3): overlapping bin j holds the fine bins j
 // and j + 1 (mod n), so the sum is over T(c_j + c_(j+1)): the first bin is
 // peeled off, each later bin pairs with the one before it, and the last pairs
 // with the first (table offsets add like the counts).  G bins of every trial
 // are loaded before any is stored, so the loads overlap.
-template <int TPT, int FMT, bool SEG, bool ALL_SMEM, bool OVL, int STRIDE>
+template <int TPT, int FMT, int KIND, bool ALL_SMEM, bool OVL, int STRIDE>
 struct Sweep {
-    typedef Fields<FMT, SEG> F;
+    typedef Fields<FMT, KIND> F;
     static constexpr int NF = F::NF;
     unsigned int *const cnt;               // the thread's counter words
     const unsigned long long *const s_tab;  // the c ln c table in shared memory
@@ -324,6 +347,10 @@ struct Sweep {
         if (ALL_SMEM) return *e;
         const int c = (int)(o >> 3);
         return c < table_smem ? *e : __ldg(g_tab + c);
+    }
+    __device__ __forceinline__ static void add(unsigned long long &t, int f, unsigned long long x) {
+        if (F::sign(f) > 0) t += x;
+        else t -= x;
     }
 
     // G bins of trial s at words cnt[w[s]], cnt[w[s] + STRIDE], ...; PEEL: the
@@ -347,10 +374,10 @@ struct Sweep {
                 for (int f = 0; f < NF; ++f) {
                     if (OVL) {
                         if (PEEL && g == 0) first[s][f] = o[f];
-                        else t[s] += look(prev[s][f] + o[f]);
+                        else add(t[s], f, look(prev[s][f] + o[f]));
                         prev[s][f] = o[f];
                     } else {
-                        t[s] += look(o[f]);
+                        add(t[s], f, look(o[f]));
                     }
                 }
             }
@@ -365,10 +392,10 @@ struct Sweep {
     }
 
     // w0[s]: word offset (from cnt) of trial s's first window slot; e: extra
-    // slots (SEG only)
+    // slots, merged first
     __device__ __forceinline__ void run(const int (&w0)[TPT], int n, int e,
                                         unsigned long long (&acc)[TPT]) {
-        if (SEG) {
+        {
             for (int i = 0, b = 0; i < e; ++i, b = (b + 1 == n) ? 0 : b + 1) {
 #pragma unroll
                 for (int s = 0; s < TPT; ++s) {
@@ -376,13 +403,14 @@ struct Sweep {
                     unsigned int *f = cnt + w0[s] + b * STRIDE;
                     const unsigned int x = *q;
                     *q = 0u;
-                    *f = merge(*f, x);
+                    *f = F::merge(*f, x);
                 }
             }
         }
         int w[TPT];
 #pragma unroll
         for (int s = 0; s < TPT; ++s) w[s] = w0[s];
+        // bins per step: about four words in flight
         constexpr int G = TPT * NF >= 4 ? 2 : 4;
         int j = 0;
         if (OVL) {
@@ -399,21 +427,15 @@ struct Sweep {
 #pragma unroll
             for (int s = 0; s < TPT; ++s)
 #pragma unroll
-                for (int f = 0; f < NF; ++f) acc[s] += look(prev[s][f] + first[s][f]);
+                for (int f = 0; f < NF; ++f) add(acc[s], f, look(prev[s][f] + first[s][f]));
         }
     }
 
-  private:
-    template <bool S = SEG>
-    __device__ __forceinline__ static unsigned int merge(unsigned int w, unsigned int x) {
-        if constexpr (S) return F::merge(w, x);
-        else return w;
-    }
 };
 
 // Dispatch of the sweeps of one work item over the run-time choices (overlapping
 // bins, whole table in shared memory).
-template <int TPT, int STRIDE>
+template <int TPT, int STRIDE, bool OVL>
 struct Sweeper {
     unsigned int *cnt;
     const unsigned long long *s_tab;
@@ -421,27 +443,11 @@ struct Sweeper {
     const unsigned long long *g_tab;
     int n;  // phase bins
 
-    template <int FMT>
-    __device__ __forceinline__ void segment(bool ovl, bool tab_all, const int (&w0)[TPT], int e,
-                                            unsigned long long (&acc)[TPT]) const {
-        if (ovl) {
-            if (tab_all) Sweep<TPT, FMT, true, true, true, STRIDE>{cnt, s_tab, table_smem, g_tab}.run(w0, n, e, acc);
-            else Sweep<TPT, FMT, true, false, true, STRIDE>{cnt, s_tab, table_smem, g_tab}.run(w0, n, e, acc);
-        } else {
-            if (tab_all) Sweep<TPT, FMT, true, true, false, STRIDE>{cnt, s_tab, table_smem, g_tab}.run(w0, n, e, acc);
-            else Sweep<TPT, FMT, true, false, false, STRIDE>{cnt, s_tab, table_smem, g_tab}.run(w0, n, e, acc);
-        }
-    }
-    template <int FMT>
-    __device__ __forceinline__ void marginal(bool ovl, bool tab_all, const int (&w0)[TPT],
-                                             unsigned long long (&acc)[TPT]) const {
-        if (ovl) {
-            if (tab_all) Sweep<TPT, FMT, false, true, true, STRIDE>{cnt, s_tab, table_smem, g_tab}.run(w0, n, 0, acc);
-            else Sweep<TPT, FMT, false, false, true, STRIDE>{cnt, s_tab, table_smem, g_tab}.run(w0, n, 0, acc);
-        } else {
-            if (tab_all) Sweep<TPT, FMT, false, true, false, STRIDE>{cnt, s_tab, table_smem, g_tab}.run(w0, n, 0, acc);
-            else Sweep<TPT, FMT, false, false, false, STRIDE>{cnt, s_tab, table_smem, g_tab}.run(w0, n, 0, acc);
-        }
+    template <int FMT, int KIND>
+    __device__ __forceinline__ void run(bool tab_all, const int (&w0)[TPT], int e,
+                                        unsigned long long (&acc)[TPT]) const {
+        if (tab_all) Sweep<TPT, FMT, KIND, true, OVL, STRIDE>{cnt, s_tab, table_smem, g_tab}.run(w0, n, e, acc);
+        else Sweep<TPT, FMT, KIND, false, OVL, STRIDE>{cnt, s_tab, table_smem, g_tab}.run(w0, n, e, acc);
     }
 };
 
@@ -662,9 +668,11 @@ __global__ void __launch_bounds__(1 << LOG2B, main_min_blocks(TPT, LOG2B)) k_mai
 #endif
         }
 
-        unsigned long long s_ij[TPT];
+        // N H 2^32 per trial (Eq. 4 as Sigma_j T(c_j) - Sigma_ij T(c_ij)), exact
+        // modulo 2^64 while it is summed, non-negative at the end
+        unsigned long long nh[TPT];
 #pragma unroll
-        for (int s = 0; s < TPT; ++s) s_ij[s] = 0ull;
+        for (int s = 0; s < TPT; ++s) nh[s] = 0ull;
 
         // FMT_PK2 (one sweep per two non-empty segments) with 50 %-overlapping
         // bins on curves of at most kPk2MaxN points, else FMT_SNAP (one sweep per
@@ -673,7 +681,7 @@ __global__ void __launch_bounds__(1 << LOG2B, main_min_blocks(TPT, LOG2B)) k_mai
         // of every other sweep, which pays with overlapping bins and costs more
         // field arithmetic than it saves without them.
         const bool pk2 = ovl && n <= kPk2MaxN;
-        const Sweeper<TPT, B> sw{my_cnt, s_tab, a.table_smem, a.table, n_phase};
+        const Sweeper<TPT, B, OVL> sw{my_cnt, s_tab, a.table_smem, a.table, n_phase};
         int ended = 0;  // non-empty segments ended so far (FMT_PK2: field = ended & 1)
         for (int lo = 0; lo < n; lo += chunk_pts) {
             const int hi = min(n, lo + chunk_pts);
@@ -715,29 +723,29 @@ __global__ void __launch_bounds__(1 << LOG2B, main_min_blocks(TPT, LOG2B)) k_mai
                 }
                 if (s1 > s0 && s1 > lo && s1 <= hi) {
                     // end of non-empty magnitude segment i: sweep its counts (FMT_PK2:
-                    // after every second one)
-                    if (!pk2) sw.segment<FMT_SNAP>(ovl, tab_all, wl, n_extra, s_ij);
-                    else if (ended & 1) sw.segment<FMT_PK2>(ovl, tab_all, wl, n_extra, s_ij);
+                    // after every second one); after the curve's last segment one sweep
+                    // takes its counts and the cumulative ones (the marginal term) and
+                    // clears the counters for the next item
+                    if (s1 == n) {
+                        if (pk2) sw.run<FMT_PK2, SW_LAST>(tab_all, wl, n_extra, nh);
+                        else sw.run<FMT_SNAP, SW_LAST>(tab_all, wl, n_extra, nh);
+                    } else if (!pk2) {
+                        sw.run<FMT_SNAP, SW_SEG>(tab_all, wl, n_extra, nh);
+                    } else if (ended & 1) {
+                        sw.run<FMT_PK2, SW_SEG>(tab_all, wl, n_extra, nh);
+                    }
                     ++ended;
                 }
             }
         }
-        if (pk2 && (ended & 1)) sw.segment<FMT_PK2>(ovl, tab_all, wl, n_extra, s_ij);  // the last, alone
 
-        // sum_j c_j ln c_j from the cumulative counters, then H (the counts total
-        // 2N with overlapping bins, every point being in two bins); this sweep
-        // clears the counters for the next item (the extra slots are already 0)
+        // H (the counts total 2N with overlapping bins, every point being in two)
         const double inv = kTabInvScale / (double)(n * (1 + ovl));
-        unsigned long long key[TPT], sjs[TPT];
+        unsigned long long key[TPT];
         float hv[TPT];
 #pragma unroll
-        for (int s = 0; s < TPT; ++s) sjs[s] = 0ull;
-        if (pk2) sw.marginal<FMT_PK2>(ovl, tab_all, wl, sjs);
-        else sw.marginal<FMT_SNAP>(ovl, tab_all, wl, sjs);
-#pragma unroll
         for (int s = 0; s < TPT; ++s) {
-            const unsigned long long sj = sjs[s];
-            long long d = (long long)(sj - s_ij[s]);
+            long long d = (long long)nh[s];
             if (d < 0) d = 0;
             const float h = __double2float_rn(__dmul_rn(__ll2double_rn(d), inv));
             hv[s] = h;
