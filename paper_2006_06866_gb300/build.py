@@ -68,7 +68,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False,
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")
         return obj, r.stderr
 
-    with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 4)) as ex:
+    with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 4)) as ex:
         for obj, log in ex.map(compile_one, _sources()):
             objs.append(obj)
             if (verbose or ptxas_info) and log:

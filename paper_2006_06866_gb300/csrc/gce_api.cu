@@ -310,7 +310,8 @@ struct Job {
 struct Plan {
     long long n_points, n_trials, n_items, n_long_items;
     int n_long, n_short;  // curves taken curve-major / tile-major (see MainArgs)
-    int n_max, n_tiles, n_ptiles, pd_major, narrow, half, block, tpt, grid, chunk, table_smem, grab;
+    int n_max, n_tiles, n_ptiles, pd_major, narrow, half, kv, block, tpt, grid, chunk, table_smem,
+        grab;
     int n_groups, tiles_per_group;  // top-k: first merge level (0 groups: none)
     size_t smem;
 };
@@ -331,9 +332,11 @@ gce_status make_plan(gce_handle h, const Job &j, Plan &pl) {
     pl.narrow = (cfg->phase_mode == GCE_PHASE_SPLIT32 && j.n_pdots > 1) ? 1 : 0;
     // one Pdot value: the SPLIT32 / FIXED32 staging holds 8-byte half points
     pl.half = (cfg->phase_mode != GCE_PHASE_FP64 && j.n_pdots == 1) ? 1 : 0;
-    const bool ovl = (cfg->flags & GCE_FLAG_OVERLAP) != 0;  // a kernel of its own
+    // the kernel instantiation: overlapping bins or not
+    pl.kv = kernel_variant((cfg->flags & GCE_FLAG_OVERLAP) != 0);
+    const int kv = pl.kv;
     const ShapeKey skey(cfg->phase_mode, cfg->n_phase_bins, cfg->n_mag_bins, pl.n_max, kk,
-                        pl.narrow * 4 + pl.half * 2 + (ovl ? 1 : 0), t.block, t.tpt, t.chunk,
+                        pl.narrow * 8 + pl.half * 4 + kv, t.block, t.tpt, t.chunk,
                         t.ctas_per_sm);
     int occ = 0;
     auto sit = h->shapes.find(skey);
@@ -360,7 +363,7 @@ gce_status make_plan(gce_handle h, const Job &j, Plan &pl) {
                                    cfg->n_mag_bins, pl.table_smem, kk, pl.narrow, pl.half);
         };
         auto limit = [&]() {
-            return main_dynamic_smem_limit(cfg->phase_mode, pl.tpt, pl.block, ovl, (size_t)h->smem_optin);
+            return main_dynamic_smem_limit(cfg->phase_mode, pl.tpt, pl.block, kv, (size_t)h->smem_optin);
         };
         pl.smem = size();
         while (pl.smem > limit()) {
@@ -374,8 +377,8 @@ gce_status make_plan(gce_handle h, const Job &j, Plan &pl) {
         }
         if (pl.smem > limit())
             return fail(h, GCE_ERR_UNSUPPORTED, "launch shape needs %zu bytes of shared memory", pl.smem);
-        CUDA_TRY(h, main_kernel_attrs(cfg->phase_mode, pl.tpt, pl.block, ovl, (size_t)h->smem_optin));
-        const void *kern = main_kernel_ptr(cfg->phase_mode, pl.tpt, pl.block, ovl);
+        CUDA_TRY(h, main_kernel_attrs(cfg->phase_mode, pl.tpt, pl.block, kv, (size_t)h->smem_optin));
+        const void *kern = main_kernel_ptr(cfg->phase_mode, pl.tpt, pl.block, kv);
         CUDA_TRY(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, pl.block, pl.smem));
         if (occ < 1) return fail(h, GCE_ERR_UNSUPPORTED, "launch shape does not fit on an SM");
         // A smaller staged chunk costs only more staging passes: take it whenever it
@@ -508,6 +511,7 @@ gce_status enqueue(gce_handle h, const Job &j, const Plan &pl, cudaStream_t s, b
     ma.stats = nullptr;
     ma.overlap = (cfg->flags & GCE_FLAG_OVERLAP) ? 1 : 0;
     ma.half = pl.half;
+    ma.kv = pl.kv;
     ma.state = st;
     const bool timed = (cfg->flags & GCE_FLAG_TIME_KERNEL) != 0;
     gce_status ms;

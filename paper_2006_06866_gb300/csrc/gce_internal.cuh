@@ -428,8 +428,15 @@ struct MainArgs {
     // half points (8 bytes); a job whose Pdot is 0 stages half points, one whose
     // single Pdot is not 0 stages chunk / 2 whole points in the same bytes
     int half;
+    int kv;                    // CE kernel variant (KV_*): overlapping bins or not
     JobState *state;
 };
+
+// Instantiations of the CE kernel: without overlapping bins (snapshot counters),
+// and with them (packed two-segment counters for curves of at most 1023 points,
+// snapshot counters for longer ones).
+enum { KV_SNAP = 0, KV_OVL = 1 };
+inline int kernel_variant(bool overlap) { return overlap ? KV_OVL : KV_SNAP; }
 
 // Kernel launchers (defined in the .cu files).
 cudaError_t launch_init(JobState *st, cudaStream_t s);
@@ -445,19 +452,23 @@ cudaError_t launch_table(unsigned long long *table, int n_max, cudaStream_t s);
 size_t main_smem_bytes(int mode, int block, int tpt, int chunk, int n_phase, int n_mag,
                        int table_smem, int k, int narrow, int half);
 size_t single_smem_bytes(int n_phase, int block);
-size_t main_dynamic_smem_limit(int mode, int tpt, int block, bool ovl, size_t smem_optin);
-cudaError_t main_kernel_attrs(int mode, int tpt, int block, bool ovl, size_t smem_optin);
-const void *main_kernel_ptr(int mode, int tpt, int block, bool ovl);
-// per fold mode (gce_main_<mode>.cu)
-const void *main_kernel_ptr_fp64(int tpt, int block, bool ovl);
-const void *main_kernel_ptr_split32(int tpt, int block, bool ovl);
-const void *main_kernel_ptr_fixed32(int tpt, int block, bool ovl);
-cudaError_t launch_main_fp64(int tpt, int block, int grid, size_t smem, const MainArgs &a,
-                             cudaStream_t s);
-cudaError_t launch_main_split32(int tpt, int block, int grid, size_t smem, const MainArgs &a,
-                                cudaStream_t s);
-cudaError_t launch_main_fixed32(int tpt, int block, int grid, size_t smem, const MainArgs &a,
-                                cudaStream_t s);
+size_t main_dynamic_smem_limit(int mode, int tpt, int block, int kv, size_t smem_optin);
+cudaError_t main_kernel_attrs(int mode, int tpt, int block, int kv, size_t smem_optin);
+const void *main_kernel_ptr(int mode, int tpt, int block, int kv);
+// per fold mode and trials per thread (gce_main_<mode>_t<tpt>.cu)
+#define GCE_MAIN_TU(name, t)                                                           \
+    const void *main_kernel_ptr_##name##_t##t(int block, int kv);                       \
+    cudaError_t launch_main_##name##_t##t(int block, int grid, size_t smem, const MainArgs &a, \
+                                          cudaStream_t s);
+GCE_MAIN_TU(fp64, 1)
+GCE_MAIN_TU(fp64, 2)
+GCE_MAIN_TU(split32, 1)
+GCE_MAIN_TU(split32, 2)
+GCE_MAIN_TU(split32, 4)
+GCE_MAIN_TU(fixed32, 1)
+GCE_MAIN_TU(fixed32, 2)
+GCE_MAIN_TU(fixed32, 4)
+#undef GCE_MAIN_TU
 cudaError_t launch_main(int mode, int tpt, int block, int grid, size_t smem,
                         const MainArgs &a, cudaStream_t s);
 cudaError_t launch_topk_merge(const unsigned long long *cand, int n_curves, int n_tiles,

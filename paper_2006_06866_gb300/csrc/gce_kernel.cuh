@@ -1,5 +1,5 @@
-// The CE kernel (included by one translation unit per fold mode, which
-// instantiate it): fold (Eq. 3) -> phase x magnitude histogram (Sec. 2.3) ->
+// The CE kernel (included by one translation unit per fold mode and trials
+// per thread, which instantiate it): fold (Eq. 3) -> phase x magnitude histogram (Sec. 2.3) ->
 // entropy (Eq. 4) -> grid or per-curve top-k (Sec. 2.3, Sec. 4).
 //
 // Work decomposition.  One thread owns TPT trials (P, Pdot) of one light curve
@@ -244,8 +244,8 @@ __device__ __forceinline__ int take_segment(unsigned int *w) {
 //     Consecutive non-empty magnitude segments alternate between the fields A
 //     (increment 1) and B (increment 1 << 10); C is the cumulative count of the
 //     segments already swept.  One sweep then serves two segments: it reads A and
-//     B, adds them to C and clears them.  No field can overflow: each is at most
-//     the curve's point count.
+//     B, adds them to C and clears them.
+// No field can overflow: each is at most the curve's point count.
 enum { FMT_SNAP = 0, FMT_PK2 = 1 };
 constexpr int kPk2MaxN = 1023;
 constexpr unsigned int kPk2IncB = 1u << 10;
@@ -506,8 +506,13 @@ constexpr int main_min_blocks(int tpt, int log2b) {
                     : (log2b >= 9 ? 1 : (log2b == 8 ? 2 : (log2b == 7 ? 4 : 8)));
 }
 
-template <int MODE, int TPT, int LOG2B, bool OVL>
+template <int MODE, int TPT, int LOG2B, int KV>
 __global__ void __launch_bounds__(1 << LOG2B, main_min_blocks(TPT, LOG2B)) k_main(MainArgs a) {
+    // the counter formats are fixed per instantiation (a kernel that carried
+    // the overlapping-bin format with a run-time choice measured slower on the
+    // path that never used it)
+    constexpr bool OVL = KV == KV_OVL;
+    constexpr int FMT = FMT_SNAP;  // without overlapping bins
     typedef typename ModeTraits<MODE>::point_t point_t;
     typedef typename ModeTraits<MODE>::trial_t trial_t;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -675,8 +680,8 @@ __global__ void __launch_bounds__(1 << LOG2B, main_min_blocks(TPT, LOG2B)) k_mai
         for (int s = 0; s < TPT; ++s) nh[s] = 0ull;
 
         // FMT_PK2 (one sweep per two non-empty segments) with 50 %-overlapping
-        // bins on curves of at most kPk2MaxN points, else FMT_SNAP (one sweep per
-        // segment).  Each count costs the same table lookup and 64-bit add in both
+        // bins on curves of at most kPk2MaxN points, else the kernel's format (one
+        // sweep per segment).  Each count costs the same table lookup and 64-bit add in both
         // formats; FMT_PK2 saves the loads, stores and the overlapping pairs' set-up
         // of every other sweep, which pays with overlapping bins and costs more
         // field arithmetic than it saves without them.
@@ -728,9 +733,9 @@ __global__ void __launch_bounds__(1 << LOG2B, main_min_blocks(TPT, LOG2B)) k_mai
                     // clears the counters for the next item
                     if (s1 == n) {
                         if (pk2) sw.run<FMT_PK2, SW_LAST>(tab_all, wl, n_extra, nh);
-                        else sw.run<FMT_SNAP, SW_LAST>(tab_all, wl, n_extra, nh);
+                        else sw.run<FMT, SW_LAST>(tab_all, wl, n_extra, nh);
                     } else if (!pk2) {
-                        sw.run<FMT_SNAP, SW_SEG>(tab_all, wl, n_extra, nh);
+                        sw.run<FMT, SW_SEG>(tab_all, wl, n_extra, nh);
                     } else if (ended & 1) {
                         sw.run<FMT_PK2, SW_SEG>(tab_all, wl, n_extra, nh);
                     }
@@ -831,32 +836,31 @@ __global__ void __launch_bounds__(1 << LOG2B, main_min_blocks(TPT, LOG2B)) k_mai
 
 template <int MODE, int TPT, int LOG2B>
 cudaError_t launch_main_t(int grid, size_t smem, const MainArgs &a, cudaStream_t s) {
-    if (a.overlap) k_main<MODE, TPT, LOG2B, true><<<grid, 1 << LOG2B, smem, s>>>(a);
-    else k_main<MODE, TPT, LOG2B, false><<<grid, 1 << LOG2B, smem, s>>>(a);
+    switch (a.kv) {
+        case KV_SNAP: k_main<MODE, TPT, LOG2B, KV_SNAP><<<grid, 1 << LOG2B, smem, s>>>(a); break;
+        case KV_OVL: k_main<MODE, TPT, LOG2B, KV_OVL><<<grid, 1 << LOG2B, smem, s>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
 // The kernel instantiations: mode x trials per thread x block size.
-template <int MODE, int TPT, bool OVL>
+template <int MODE, int TPT, int KV>
 const void *kernel_for_block(int block) {
     switch (block) {
-        case 64: return (const void *)k_main<MODE, TPT, 6, OVL>;
-        case 128: return (const void *)k_main<MODE, TPT, 7, OVL>;
-        case 256: return (const void *)k_main<MODE, TPT, 8, OVL>;
-        case 512: return (const void *)k_main<MODE, TPT, 9, OVL>;
+        case 64: return (const void *)k_main<MODE, TPT, 6, KV>;
+        case 128: return (const void *)k_main<MODE, TPT, 7, KV>;
+        case 256: return (const void *)k_main<MODE, TPT, 8, KV>;
+        case 512: return (const void *)k_main<MODE, TPT, 9, KV>;
         default: return nullptr;
     }
 }
 
-// The mode's kernel for (trials per thread, block, overlapping bins).
-template <int MODE>
-const void *mode_kernel_ptr(int tpt, int block, bool ovl) {
-    switch (tpt) {
-        case 1: return ovl ? kernel_for_block<MODE, 1, true>(block) : kernel_for_block<MODE, 1, false>(block);
-        case 2: return ovl ? kernel_for_block<MODE, 2, true>(block) : kernel_for_block<MODE, 2, false>(block);
-        case 4:
-            if (MODE == GCE_PHASE_FP64) return nullptr;  // not built
-            return ovl ? kernel_for_block<MODE, 4, true>(block) : kernel_for_block<MODE, 4, false>(block);
+template <int MODE, int TPT>
+const void *kernel_for_variant(int block, int kv) {
+    switch (kv) {
+        case KV_SNAP: return kernel_for_block<MODE, TPT, KV_SNAP>(block);
+        case KV_OVL: return kernel_for_block<MODE, TPT, KV_OVL>(block);
         default: return nullptr;
     }
 }
@@ -868,19 +872,6 @@ cudaError_t launch_for_block(int block, int grid, size_t smem, const MainArgs &a
         case 128: return launch_main_t<MODE, TPT, 7>(grid, smem, a, s);
         case 256: return launch_main_t<MODE, TPT, 8>(grid, smem, a, s);
         case 512: return launch_main_t<MODE, TPT, 9>(grid, smem, a, s);
-        default: return cudaErrorInvalidValue;
-    }
-}
-
-template <int MODE>
-cudaError_t mode_launch(int tpt, int block, int grid, size_t smem, const MainArgs &a,
-                        cudaStream_t s) {
-    switch (tpt) {
-        case 1: return launch_for_block<MODE, 1>(block, grid, smem, a, s);
-        case 2: return launch_for_block<MODE, 2>(block, grid, smem, a, s);
-        case 4:
-            if (MODE == GCE_PHASE_FP64) return cudaErrorInvalidValue;  // not built
-            return launch_for_block<MODE, 4>(block, grid, smem, a, s);
         default: return cudaErrorInvalidValue;
     }
 }

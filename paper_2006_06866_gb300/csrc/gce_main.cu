@@ -1,7 +1,7 @@
 // The kernels around the CE kernel: per-curve top-k merge (and the Eq. 5
 // moments), the plain one-launch-per-curve FP64 baseline, diagnostic counts,
 // and the dispatch of the CE kernel's instantiations (one translation unit per
-// fold mode: gce_main_fp64.cu, gce_main_split32.cu, gce_main_fixed32.cu).
+// fold mode and trials per thread: gce_main_<mode>_t<tpt>.cu).
 #include "gce_kernel.cuh"
 
 namespace gce {
@@ -148,19 +148,24 @@ size_t main_smem_bytes(int mode, int block, int tpt, int chunk, int n_phase, int
 
 size_t single_smem_bytes(int n_phase, int block) { return 4 * (size_t)n_phase * block; }
 
-const void *main_kernel_ptr(int mode, int tpt, int block, bool ovl) {
-    switch (mode) {
-        case GCE_PHASE_FP64: return main_kernel_ptr_fp64(tpt, block, ovl);
-        case GCE_PHASE_SPLIT32: return main_kernel_ptr_split32(tpt, block, ovl);
-        case GCE_PHASE_FIXED32: return main_kernel_ptr_fixed32(tpt, block, ovl);
+const void *main_kernel_ptr(int mode, int tpt, int block, int kv) {
+    switch (mode * 8 + tpt) {
+        case GCE_PHASE_FP64 * 8 + 1: return main_kernel_ptr_fp64_t1(block, kv);
+        case GCE_PHASE_FP64 * 8 + 2: return main_kernel_ptr_fp64_t2(block, kv);
+        case GCE_PHASE_SPLIT32 * 8 + 1: return main_kernel_ptr_split32_t1(block, kv);
+        case GCE_PHASE_SPLIT32 * 8 + 2: return main_kernel_ptr_split32_t2(block, kv);
+        case GCE_PHASE_SPLIT32 * 8 + 4: return main_kernel_ptr_split32_t4(block, kv);
+        case GCE_PHASE_FIXED32 * 8 + 1: return main_kernel_ptr_fixed32_t1(block, kv);
+        case GCE_PHASE_FIXED32 * 8 + 2: return main_kernel_ptr_fixed32_t2(block, kv);
+        case GCE_PHASE_FIXED32 * 8 + 4: return main_kernel_ptr_fixed32_t4(block, kv);
         default: return nullptr;
     }
 }
 
 // The dynamic shared memory a CTA of the kernel can have: the device's opt-in
 // maximum less the kernel's static shared memory (0 if the kernel is unknown).
-size_t main_dynamic_smem_limit(int mode, int tpt, int block, bool ovl, size_t smem_optin) {
-    const void *f = main_kernel_ptr(mode, tpt, block, ovl);
+size_t main_dynamic_smem_limit(int mode, int tpt, int block, int kv, size_t smem_optin) {
+    const void *f = main_kernel_ptr(mode, tpt, block, kv);
     cudaFuncAttributes fa;
     if (!f || cudaFuncGetAttributes(&fa, f) != cudaSuccess || fa.sharedSizeBytes > smem_optin) {
         cudaGetLastError();
@@ -172,20 +177,25 @@ size_t main_dynamic_smem_limit(int mode, int tpt, int block, bool ovl, size_t sm
 // The kernel's dynamic shared-memory limit is raised to that maximum, never set
 // to one job's size, so that calls planned on other host threads (which all set
 // the same value) cannot lower it between their planning and their launch.
-cudaError_t main_kernel_attrs(int mode, int tpt, int block, bool ovl, size_t smem_optin) {
-    const void *f = main_kernel_ptr(mode, tpt, block, ovl);
+cudaError_t main_kernel_attrs(int mode, int tpt, int block, int kv, size_t smem_optin) {
+    const void *f = main_kernel_ptr(mode, tpt, block, kv);
     if (!f) return cudaErrorInvalidValue;
-    const size_t lim = main_dynamic_smem_limit(mode, tpt, block, ovl, smem_optin);
+    const size_t lim = main_dynamic_smem_limit(mode, tpt, block, kv, smem_optin);
     if (lim == 0) return cudaErrorInvalidValue;
     return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim);
 }
 
 cudaError_t launch_main(int mode, int tpt, int block, int grid, size_t smem, const MainArgs &a,
                         cudaStream_t s) {
-    switch (mode) {
-        case GCE_PHASE_FP64: return launch_main_fp64(tpt, block, grid, smem, a, s);
-        case GCE_PHASE_SPLIT32: return launch_main_split32(tpt, block, grid, smem, a, s);
-        case GCE_PHASE_FIXED32: return launch_main_fixed32(tpt, block, grid, smem, a, s);
+    switch (mode * 8 + tpt) {
+        case GCE_PHASE_FP64 * 8 + 1: return launch_main_fp64_t1(block, grid, smem, a, s);
+        case GCE_PHASE_FP64 * 8 + 2: return launch_main_fp64_t2(block, grid, smem, a, s);
+        case GCE_PHASE_SPLIT32 * 8 + 1: return launch_main_split32_t1(block, grid, smem, a, s);
+        case GCE_PHASE_SPLIT32 * 8 + 2: return launch_main_split32_t2(block, grid, smem, a, s);
+        case GCE_PHASE_SPLIT32 * 8 + 4: return launch_main_split32_t4(block, grid, smem, a, s);
+        case GCE_PHASE_FIXED32 * 8 + 1: return launch_main_fixed32_t1(block, grid, smem, a, s);
+        case GCE_PHASE_FIXED32 * 8 + 2: return launch_main_fixed32_t2(block, grid, smem, a, s);
+        case GCE_PHASE_FIXED32 * 8 + 4: return launch_main_fixed32_t4(block, grid, smem, a, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -1,0 +1,17 @@
+// Instantiations of the CE kernel for the FP64 fold with 2 trials per
+// thread (one translation unit per fold mode and trials per thread, so that
+// they compile in parallel).
+#include "gce_kernel.cuh"
+
+namespace gce {
+
+const void *main_kernel_ptr_fp64_t2(int block, int kv) {
+    return kernel_for_variant<GCE_PHASE_FP64, 2>(block, kv);
+}
+
+cudaError_t launch_main_fp64_t2(int block, int grid, size_t smem, const MainArgs &a,
+                                  cudaStream_t s) {
+    return launch_for_block<GCE_PHASE_FP64, 2>(block, grid, smem, a, s);
+}
+
+}  // namespace gce

@@ -171,8 +171,8 @@ extern "C" gce_status gce_ce_topk_static(const double *times, const double *mags
     const int half = (mode != GCE_PHASE_FP64 && n_pdots == 1) ? 1 : 0;
     const size_t smem = main_smem_bytes(mode, block, tpt, chunk, cfg->n_phase_bins,
                                         cfg->n_mag_bins, table_smem, k, narrow, half);
-    const bool ovl = (cfg->flags & GCE_FLAG_OVERLAP) != 0;
-    if (smem > main_dynamic_smem_limit(mode, tpt, block, ovl, (size_t)d->smem_optin))
+    const int kv = kernel_variant((cfg->flags & GCE_FLAG_OVERLAP) != 0);
+    if (smem > main_dynamic_smem_limit(mode, tpt, block, kv, (size_t)d->smem_optin))
         return fail(GCE_ERR_UNSUPPORTED, "bin counts too large for this entry point");
     const TileGrid tg = tile_grid(n_periods, n_pdots, block, tpt);
     const long long n_tiles = tg.n_tiles;
@@ -181,10 +181,10 @@ extern "C" gce_status gce_ce_topk_static(const double *times, const double *mags
     if (L.end > kScratchBytes)
         return fail(GCE_ERR_NOMEM, "job needs more than the 32 MiB of built-in scratch");
 
-    e = main_kernel_attrs(mode, tpt, block, ovl, (size_t)d->smem_optin);
+    e = main_kernel_attrs(mode, tpt, block, kv, (size_t)d->smem_optin);
     if (e != cudaSuccess) return fail(GCE_ERR_CUDA, cudaGetErrorString(e));
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, main_kernel_ptr(mode, tpt, block, ovl), block, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, main_kernel_ptr(mode, tpt, block, kv), block, smem);
     if (e != cudaSuccess || occ < 1) return fail(GCE_ERR_CUDA, "occupancy query failed");
     const long long n_items = (long long)n_curves * n_tiles;
     long long grid = (long long)d->n_sm * occ;
@@ -253,6 +253,7 @@ extern "C" gce_status gce_ce_topk_static(const double *times, const double *mags
     ma.stats = nullptr;
     ma.overlap = (cfg->flags & GCE_FLAG_OVERLAP) ? 1 : 0;
     ma.half = half;
+    ma.kv = kv;
     ma.state = state;
     if ((e = launch_main(mode, tpt, block, (int)grid, smem, ma, s)) != cudaSuccess)
         return fail(GCE_ERR_CUDA, cudaGetErrorString(e));
