@@ -14,11 +14,13 @@
 //
 // Counters.  One 32-bit shared-memory word per (trial, phase slot), private to
 // its thread and laid out [trial][slot][thread] so a warp's accesses fall in
-// distinct banks.  The low 16 bits count points (N <= 65535); the high 16 bits
-// hold a snapshot taken at the end of the previous magnitude segment, so the
-// segment's c_ij is low - high.  Points are counted with a shared-memory atomic
-// add whose result is unused: it needs no read-modify-write round trip in the
-// thread, and no other thread touches the word.
+// distinct banks.  Without overlapping bins the low 16 bits count points
+// (N <= 65535) and the high 16 bits hold a snapshot taken at the end of the
+// previous magnitude segment, so the segment's c_ij is low - high; with them,
+// short curves pack two segments' counts and the cumulative count into the word
+// (FMT_PK2 below).  Points are counted with a shared-memory atomic add whose
+// result is unused: it needs no read-modify-write round trip in the thread, and
+// no other thread touches the word.
 //
 // Entropy.  N H = sum_j c_j ln c_j - sum_ij c_ij ln c_ij, accumulated as exact
 // 64-bit integers from a fixed-point c ln c table (2^32 scale); H is converted
@@ -433,8 +435,9 @@ struct Sweep {
 
 };
 
-// Dispatch of the sweeps of one work item over the run-time choices (overlapping
-// bins, whole table in shared memory).
+// Dispatch of one work item's sweeps over the run-time choice of where the c ln c
+// table is read (whole in shared memory, or shared below table_smem and global
+// above).
 template <int TPT, int STRIDE, bool OVL>
 struct Sweeper {
     unsigned int *cnt;
