@@ -85,7 +85,6 @@ def profiled_traffic(mode, workload, n_curves):
     """DRAM bytes per full launch of k_main recorded under profiles/ for the batch
     workload, or None when the kernel sources changed since that capture (their
     hash no longer matches) or the run is not that workload."""
-    import hashlib
     prof = os.path.join(ROOT, "profiles", f"k_main_{mode}_batch_100curves.md")
     if workload != 1 or n_curves != 1000 or not os.path.exists(prof):
         return None
@@ -95,13 +94,25 @@ def profiled_traffic(mode, workload, n_curves):
                                                   "kernel_sources_sha256_16"):
             k, v = line.split(":", 1)
             rec[k.strip()] = v.strip()
-    h = hashlib.sha256()
-    for f in ("gce_kernel.cuh", "gce_internal.cuh"):
-        with open(os.path.join(ROOT, "paper_2006_06866_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
-    if rec.get("kernel_sources_sha256_16") != h.hexdigest()[:16]:
+    if rec.get("kernel_sources_sha256_16") != kernel_code_hash():
         return None
     return int(rec["traffic_bytes_full_launch"]) if "traffic_bytes_full_launch" in rec else None
+
+
+def kernel_code_hash():
+    """SHA-256 (first 16 hex digits) of the CE kernel's sources with comments and
+    blank lines removed, so that a comment-only edit keeps a capture valid."""
+    import hashlib
+    import re
+    h = hashlib.sha256()
+    for f in ("gce_kernel.cuh", "gce_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2006_06866_gb300", "csrc", f)) as fh:
+            text = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
+        for line in text.splitlines():
+            line = line.split("//", 1)[0].rstrip()
+            if line.strip():
+                h.update((line + "\n").encode())
+    return h.hexdigest()[:16]
 
 
 def workload_overrides(args):
