@@ -309,6 +309,7 @@ struct Job {
 
 struct Plan {
     long long n_points, n_trials, n_items, n_long_items;
+    long long n_lists;    // top-k candidate lists (and moment records) per curve: tiles x warps
     int n_long, n_short;  // curves taken curve-major / tile-major (see MainArgs)
     int n_max, n_tiles, n_ptiles, pd_major, narrow, half, kv, block, tpt, grid, chunk, table_smem,
         grab;
@@ -360,7 +361,7 @@ gce_status make_plan(gce_handle h, const Job &j, Plan &pl) {
         // block, until the CTA fits in shared memory
         auto size = [&]() {
             return main_smem_bytes(cfg->phase_mode, pl.block, pl.tpt, pl.chunk, cfg->n_phase_bins,
-                                   cfg->n_mag_bins, pl.table_smem, kk, pl.narrow, pl.half);
+                                   cfg->n_mag_bins, pl.table_smem, pl.narrow, pl.half);
         };
         auto limit = [&]() {
             return main_dynamic_smem_limit(cfg->phase_mode, pl.tpt, pl.block, kv, (size_t)h->smem_optin);
@@ -419,7 +420,9 @@ gce_status make_plan(gce_handle h, const Job &j, Plan &pl) {
         if (j.h_offsets[c + 1] - j.h_offsets[c] <= kShortCurve) ++pl.n_short;
     pl.n_long = j.n_curves - pl.n_short;
     pl.n_long_items = (long long)pl.n_long * pl.n_tiles;
-    pl.n_groups = j.kind == JOB_TOPK ? topk_groups(pl.n_tiles, j.k, &pl.tiles_per_group) : 0;
+    // each warp of a tile writes its own candidate list and moments
+    pl.n_lists = (long long)pl.n_tiles * (pl.block / 32);
+    pl.n_groups = j.kind == JOB_TOPK ? topk_groups(pl.n_lists, j.k, &pl.tiles_per_group) : 0;
     if (j.kind != JOB_TOPK) pl.tiles_per_group = 0;
     if (t.ctas_per_sm > 0) occ = std::min(occ, t.ctas_per_sm);
     long long g = (long long)h->n_sm * occ;
@@ -535,7 +538,7 @@ gce_status enqueue(gce_handle h, const Job &j, const Plan &pl, cudaStream_t s, b
                 // many tiles per curve: reduce groups of tiles first, then merge the groups
                 TileStats *stats2 = j.rho ? (TileStats *)h->stats2.p : nullptr;
                 CUDA_TRY(h, launch_topk_reduce((const unsigned long long *)h->cand.p, j.n_curves,
-                                               pl.n_tiles, j.k, pl.tiles_per_group, pl.n_groups,
+                                               (int)pl.n_lists, j.k, pl.tiles_per_group, pl.n_groups,
                                                ma.stats, (unsigned long long *)h->cand2.p, stats2,
                                                st, s));
                 CUDA_TRY(h, launch_topk_merge((const unsigned long long *)h->cand2.p, j.n_curves,
@@ -544,7 +547,7 @@ gce_status enqueue(gce_handle h, const Job &j, const Plan &pl, cudaStream_t s, b
                 n_launch += 2;
             } else {
                 CUDA_TRY(h, launch_topk_merge((const unsigned long long *)h->cand.p, j.n_curves,
-                                              pl.n_tiles, j.k, j.topk_H, (long long *)j.topk_idx,
+                                              (int)pl.n_lists, j.k, j.topk_H, (long long *)j.topk_idx,
                                               ma.stats, j.mean, j.std_dev, j.rho, st, s));
                 ++n_launch;
             }
@@ -634,10 +637,10 @@ gce_status run_job(gce_handle h, const Job &j, cudaStream_t s) {
         (st = ensure(h, h->band_stats, sizeof(double2) * (size_t)j.n_curves * j.n_bands)) != GCE_OK)
         return st;
     if (j.kind == JOB_TOPK &&
-        (st = ensure(h, h->cand, 8 * (size_t)j.n_curves * pl.n_tiles * j.k)) != GCE_OK)
+        (st = ensure(h, h->cand, 8 * (size_t)j.n_curves * pl.n_lists * j.k)) != GCE_OK)
         return st;
     if (j.kind == JOB_TOPK && j.rho &&
-        (st = ensure(h, h->stats, sizeof(TileStats) * (size_t)j.n_curves * pl.n_tiles)) != GCE_OK)
+        (st = ensure(h, h->stats, sizeof(TileStats) * (size_t)j.n_curves * pl.n_lists)) != GCE_OK)
         return st;
     if (j.kind == JOB_TOPK && pl.n_groups > 0 &&
         (st = ensure(h, h->cand2, 8 * (size_t)j.n_curves * pl.n_groups * j.k)) != GCE_OK)

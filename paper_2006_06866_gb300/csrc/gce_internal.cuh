@@ -312,25 +312,22 @@ __host__ __device__ inline int slots_per_trial(int mode, int n_phase, bool narro
 // Byte offsets of the CE kernel's dynamic shared-memory regions, in order: the
 // c ln c table (an even number of 8-byte entries, so the points after it stay
 // 16-byte aligned), the staged points (8 bytes each for FP64 and for half
-// points, else 16; chunk is a multiple of 32), the counters, the segment starts
-// (an even count, so the 8-byte keys after them stay aligned), the top-k keys
-// and the moments.  The host sizes the launch with `total` and the kernel
-// carves its memory with the same offsets.
+// points, else 16; chunk is a multiple of 32), the counters and the segment
+// starts.  The host sizes the launch with `total` and the kernel carves its
+// memory with the same offsets.  (k and block do not enter: each warp writes its
+// top-k keys and moments straight to global memory.)
 struct MainSmemLayout {
-    unsigned int pts, cnt, seg, top, stat, total;
+    unsigned int pts, cnt, seg, total;
 };
 __host__ __device__ inline MainSmemLayout main_smem_layout(int mode, int block, int tpt, int chunk,
                                                            int n_phase, int n_mag,
-                                                           int table_smem, int k, int narrow,
-                                                           int half) {
+                                                           int table_smem, int narrow, int half) {
     MainSmemLayout L;
     const unsigned int pt = (mode == GCE_PHASE_FP64 || half) ? 8u : 16u;
     L.pts = 8u * (unsigned int)((table_smem + 1) & ~1);
     L.cnt = L.pts + pt * (unsigned int)chunk;
     L.seg = L.cnt + 4u * (unsigned int)(tpt * slots_per_trial(mode, n_phase, narrow != 0) * block);
-    L.top = L.seg + 4u * (unsigned int)((n_mag + 2) & ~1);
-    L.stat = L.top + 8u * (unsigned int)((block / 32) * (k > 0 ? k : 1));
-    L.total = L.stat + 24u * (unsigned int)(block / 32);
+    L.total = L.seg + 4u * (unsigned int)(n_mag + 1);
     return L;
 }
 
@@ -450,7 +447,7 @@ cudaError_t launch_band_stats(const double *mags, const unsigned char *bands,
                               double2 *stats, JobState *st, cudaStream_t s);
 cudaError_t launch_table(unsigned long long *table, int n_max, cudaStream_t s);
 size_t main_smem_bytes(int mode, int block, int tpt, int chunk, int n_phase, int n_mag,
-                       int table_smem, int k, int narrow, int half);
+                       int table_smem, int narrow, int half);
 size_t single_smem_bytes(int n_phase, int block);
 size_t main_dynamic_smem_limit(int mode, int tpt, int block, int kv, size_t smem_optin);
 cudaError_t main_kernel_attrs(int mode, int tpt, int block, int kv, size_t smem_optin);

@@ -538,13 +538,11 @@ __global__ void __launch_bounds__(1 << LOG2B, main_min_blocks(TPT, LOG2B)) k_mai
     // the regions at the offsets the host sized the launch with (the table first,
     // so that its address is a constant)
     const MainSmemLayout lay = main_smem_layout(MODE, B, TPT, a.chunk, n_phase, n_mag, a.table_smem,
-                                                a.k, narrow ? 1 : 0, a.half);
+                                                narrow ? 1 : 0, a.half);
     unsigned long long *s_tab = reinterpret_cast<unsigned long long *>(smem);
     point_t *s_pts = reinterpret_cast<point_t *>(smem + lay.pts);
     unsigned int *s_cnt = reinterpret_cast<unsigned int *>(smem + lay.cnt);
     int *s_seg = reinterpret_cast<int *>(smem + lay.seg);
-    unsigned long long *s_top = reinterpret_cast<unsigned long long *>(smem + lay.top);
-    double *s_stat = reinterpret_cast<double *>(smem + lay.stat);
 
     for (int i = tid; i < a.table_smem; i += B) s_tab[i] = a.table[i];
 
@@ -650,8 +648,9 @@ __global__ void __launch_bounds__(1 << LOG2B, main_min_blocks(TPT, LOG2B)) k_mai
                 tc[s] = Fold<MODE>::prepare(tr);
                 all_k0 &= Fold<MODE>::k_zero(tc[s]);
             }
-            pdot = __syncthreads_or(any_pdot) != 0;
-            k0 = MODE != GCE_PHASE_FIXED32 || __syncthreads_and(all_k0) != 0;
+            // the fold variant is chosen per warp (a warp vote, no CTA barrier)
+            pdot = __any_sync(0xffffffffu, any_pdot);
+            k0 = MODE != GCE_PHASE_FIXED32 || __all_sync(0xffffffffu, all_k0);
             // live logical slots [L, R] of this warp's counters (warp-uniform)
             int L = 0, R = n_phase - 1;
             if (SPLIT) {
@@ -764,10 +763,14 @@ __global__ void __launch_bounds__(1 << LOG2B, main_min_blocks(TPT, LOG2B)) k_mai
             }
         }
 
+        // each warp writes its own candidate list and moments (list index: curve,
+        // tile, warp), so the tile needs no barrier; the merge kernels take B / 32
+        // lists per tile
+        const long long list = ((long long)c * a.n_tiles + tile) * (B >> 5) + warp;
         if (a.stats) {
-            // moments of the tile's H for the significance of Eq. 5: per warp, sums of
-            // H - shift in FP32 (shift = lane 0's first value, so the sums stay small),
-            // then (count, mean, M2) in FP64, merged over the warps in order
+            // moments of the warp's H for the significance of Eq. 5: sums of H - shift
+            // in FP32 (shift = lane 0's first value, so the sums stay small), then
+            // (count, mean, M2) in FP64
             const float shift = __shfl_sync(0xffffffffu, hv[0], 0);
             float s1 = 0.f, s2 = 0.f, cnt = 0.f;
 #pragma unroll
@@ -786,50 +789,25 @@ __global__ void __launch_bounds__(1 << LOG2B, main_min_blocks(TPT, LOG2B)) k_mai
             }
             if (lane == 0) {
                 const double nw = cnt;
-                const double mu = nw > 0 ? (double)shift + (double)s1 / nw : 0.0;
-                const double m2 = nw > 0 ? fmax((double)s2 - (double)s1 * (double)s1 / nw, 0.0) : 0.0;
-                s_stat[3 * warp] = nw;
-                s_stat[3 * warp + 1] = mu;
-                s_stat[3 * warp + 2] = m2;
-            }
-            __syncthreads();
-            if (tid == 0) {
-                double nn = 0.0, mu = 0.0, m2 = 0.0;
-                for (int w = 0; w < (B >> 5); ++w)
-                    chan_merge(nn, mu, m2, s_stat[3 * w], s_stat[3 * w + 1], s_stat[3 * w + 2]);
-                TileStats *t = a.stats + (long long)c * a.n_tiles + tile;
-                t->n = nn;
-                t->mean = mu;
-                t->m2 = m2;
+                TileStats *t = a.stats + list;
+                t->n = nw;
+                t->mean = nw > 0 ? (double)shift + (double)s1 / nw : 0.0;
+                t->m2 = nw > 0 ? fmax((double)s2 - (double)s1 * (double)s1 / nw, 0.0) : 0.0;
             }
         }
 
         if (a.cand) {
-            // tile top-k: k rounds of warp minima, then one warp merges the warps' lists
-            const int nw = B >> 5;
+            // the warp's k smallest keys: k rounds of warp minima
+            unsigned long long *dst = a.cand + list * a.k;
             for (int r = 0; r < a.k; ++r) {
                 unsigned long long mine = key[0];
 #pragma unroll
                 for (int s = 1; s < TPT; ++s) mine = key[s] < mine ? key[s] : mine;
                 const unsigned long long m = warp_min_key(mine);
-                if (lane == 0) s_top[warp * a.k + r] = m;
+                if (lane == 0) dst[r] = m;
 #pragma unroll
                 for (int s = 0; s < TPT; ++s)
                     if (key[s] == m) key[s] = kNoKey;
-            }
-            __syncthreads();
-            if (warp == 0) {
-                unsigned long long *dst = a.cand + ((long long)c * a.n_tiles + tile) * a.k;
-                const int tot = nw * a.k;
-                for (int r = 0; r < a.k; ++r) {
-                    unsigned long long mine = kNoKey;
-                    for (int i = lane; i < tot; i += 32) mine = s_top[i] < mine ? s_top[i] : mine;
-                    const unsigned long long m = warp_min_key(mine);
-                    for (int i = lane; i < tot; i += 32)
-                        if (s_top[i] == m) s_top[i] = kNoKey;
-                    __syncwarp();
-                    if (lane == 0) dst[r] = m;
-                }
             }
         }
         ++item;

@@ -69,7 +69,7 @@ struct Layout {
 };
 
 Layout layout(long long n_points, int n_curves, long long n_trials, int n_mag, int point_bytes,
-              long long n_tiles, int k) {
+              long long n_lists, int k) {
     Layout L;
     size_t o = align256(8 * kTableEntries);
     L.state = o;
@@ -85,7 +85,7 @@ Layout layout(long long n_points, int n_curves, long long n_trials, int n_mag, i
     L.payload = o;
     o = align256(o + (size_t)point_bytes * (size_t)n_points);
     L.cand = o;
-    o = align256(o + 8 * (size_t)n_curves * (size_t)n_tiles * (size_t)k);
+    o = align256(o + 8 * (size_t)n_curves * (size_t)n_lists * (size_t)k);
     L.end = o;
     return L;
 }
@@ -170,14 +170,15 @@ extern "C" gce_status gce_ce_topk_static(const double *times, const double *mags
     const int narrow = (mode == GCE_PHASE_SPLIT32 && n_pdots > 1) ? 1 : 0;
     const int half = (mode != GCE_PHASE_FP64 && n_pdots == 1) ? 1 : 0;
     const size_t smem = main_smem_bytes(mode, block, tpt, chunk, cfg->n_phase_bins,
-                                        cfg->n_mag_bins, table_smem, k, narrow, half);
+                                        cfg->n_mag_bins, table_smem, narrow, half);
     const int kv = kernel_variant((cfg->flags & GCE_FLAG_OVERLAP) != 0);
     if (smem > main_dynamic_smem_limit(mode, tpt, block, kv, (size_t)d->smem_optin))
         return fail(GCE_ERR_UNSUPPORTED, "bin counts too large for this entry point");
     const TileGrid tg = tile_grid(n_periods, n_pdots, block, tpt);
     const long long n_tiles = tg.n_tiles;
     const int point_bytes = mode == GCE_PHASE_FP64 ? 8 : 16;
-    const Layout L = layout(n_points, n_curves, n_trials, cfg->n_mag_bins, point_bytes, n_tiles, k);
+    const long long n_lists = n_tiles * (block / 32);  // one candidate list per warp and tile
+    const Layout L = layout(n_points, n_curves, n_trials, cfg->n_mag_bins, point_bytes, n_lists, k);
     if (L.end > kScratchBytes)
         return fail(GCE_ERR_NOMEM, "job needs more than the 32 MiB of built-in scratch");
 
@@ -257,7 +258,7 @@ extern "C" gce_status gce_ce_topk_static(const double *times, const double *mags
     ma.state = state;
     if ((e = launch_main(mode, tpt, block, (int)grid, smem, ma, s)) != cudaSuccess)
         return fail(GCE_ERR_CUDA, cudaGetErrorString(e));
-    e = launch_topk_merge(ma.cand, n_curves, (int)n_tiles, k, topk_H, (long long *)topk_idx,
+    e = launch_topk_merge(ma.cand, n_curves, (int)n_lists, k, topk_H, (long long *)topk_idx,
                           nullptr, nullptr, nullptr, nullptr, state, s);
     if (e != cudaSuccess) return fail(GCE_ERR_CUDA, cudaGetErrorString(e));
     // device-side input checks: read the flags into host stack memory and wait

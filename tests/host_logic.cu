@@ -104,9 +104,8 @@ static void check_slot_range() {
 
 // The CE kernel's shared-memory layout (one function for the host's launch size
 // and the kernel's carve-up): regions in order, each aligned for its type (16
-// bytes for the staged points and the counters after them, 8 for the keys and
-// moments), the staged points sized 8 or 16 bytes each, and the total the sum
-// of the parts.
+// bytes for the staged points and the counters after them), the staged points
+// sized 8 or 16 bytes each, and the total the sum of the parts.
 static void check_smem_layout(std::mt19937_64 &rng) {
     const int blocks[] = {64, 128, 256, 512};
     const int tpts[] = {1, 2, 4};
@@ -115,19 +114,16 @@ static void check_smem_layout(std::mt19937_64 &rng) {
         const int chunk = 32 * (1 + (int)(rng() % 256));
         const int n_phase = 1 + (int)(rng() % GCE_MAX_PHASE_BINS);
         const int n_mag = 1 + (int)(rng() % GCE_MAX_MAG_BINS);
-        const int table = 1 + (int)(rng() % 2048), k = (int)(rng() % (GCE_MAX_TOPK + 1));
+        const int table = 1 + (int)(rng() % 2048);
         const int narrow = (int)(rng() % 2), half = (int)(rng() % 2);
         const MainSmemLayout L =
-            main_smem_layout(mode, B, T, chunk, n_phase, n_mag, table, k, narrow, half);
+            main_smem_layout(mode, B, T, chunk, n_phase, n_mag, table, narrow, half);
         const unsigned int pt = (mode == GCE_PHASE_FP64 || half) ? 8u : 16u;
         const unsigned int cnt = 4u * (unsigned int)(T * slots_per_trial(mode, n_phase, narrow != 0) * B);
         CHECK(L.pts >= 8u * (unsigned int)table && L.pts % 16 == 0, "pts %u table %d", L.pts, table);
         CHECK(L.cnt == L.pts + pt * (unsigned int)chunk && L.cnt % 16 == 0, "cnt %u", L.cnt);
-        CHECK(L.seg == L.cnt + cnt, "seg %u", L.seg);
-        CHECK(L.top >= L.seg + 4u * (unsigned int)(n_mag + 1) && L.top % 8 == 0, "top %u", L.top);
-        CHECK(L.stat == L.top + 8u * (unsigned int)((B / 32) * (k > 0 ? k : 1)) && L.stat % 8 == 0,
-              "stat %u", L.stat);
-        CHECK(L.total == L.stat + 24u * (unsigned int)(B / 32), "total %u", L.total);
+        CHECK(L.seg == L.cnt + cnt && L.seg % 4 == 0, "seg %u", L.seg);
+        CHECK(L.total == L.seg + 4u * (unsigned int)(n_mag + 1), "total %u", L.total);
     }
 }
 
