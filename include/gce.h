@@ -115,7 +115,7 @@ typedef struct gce_handle_s *gce_handle;
  * captured CUDA graphs.  *h is NULL on failure.
  * The workspace grows to the largest job seen and is kept until gce_destroy:
  * 8 (FP64) or 16 bytes per point, 16 (FP64, SPLIT32) or 32 (FIXED32) bytes per
- * (P, Pdot) trial, 8 k bytes per (curve, trial tile) for top-k (24 more with
+ * (P, Pdot) trial, 8 k bytes per (curve, warp of a trial tile) for top-k (24 more with
  * the significance), and 8 bytes per entry of the c ln c table (longest curve
  * + 1).  A grid of 5,183,995 periods x 512 Pdot values thus holds 42 GB of
  * trial constants in SPLIT32.  Growing a buffer waits for the device. */
@@ -227,8 +227,8 @@ gce_status gce_ce_topk_host(gce_handle h, const double *h_times, const double *h
  * (GCE_ERR_INVALID otherwise).  The call is synchronous on `stream` and folds
  * the device-side input checks into its status.
  * Returns GCE_ERR_NOMEM, launching nothing, when the job needs more than the
- * 32 MiB (about 16 B per point + 32 B per trial + 8 B per (curve, 512-trial
- * tile, k) + 0.5 MiB); use gce_ce_topk for larger jobs.  Returns
+ * 32 MiB (about 16 B per point + 32 B per trial + 8 B per (curve, 64 trials,
+ * k) + 0.5 MiB); use gce_ce_topk for larger jobs.  Returns
  * GCE_ERR_UNSUPPORTED when the bin counts need more shared memory than one CTA
  * of its fixed launch shape (256 threads, 2 trials each) can have.
  * Every call looks up the array's device address; the first call on a device

@@ -1,6 +1,6 @@
 // First level of the per-curve top-k merge.  The persistent CE kernel leaves k
-// candidate keys per (curve, trial tile); a grid of 5e6 periods x 512 Pdot
-// values has millions of tiles per curve, and one block per curve scanning them
+// candidate keys per (curve, trial tile, warp) -- a "tile" below is one such
+// list; a grid of 5e6 periods x 512 Pdot values has millions per curve, and one block per curve scanning them
 // k times would leave the rest of the GPU idle.  Here many blocks per curve
 // each stage one group of tiles' keys in shared memory once, keep its k
 // smallest, and merge the group's tile moments (Eq. 5), so that the final
