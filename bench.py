@@ -77,7 +77,8 @@ def parse():
                     help="override the Pdot-axis length of workloads 2, 4 and 5 (Sec. 3 runs "
                          "32, 128 and 512; 0 = the workload's)")
     ap.add_argument("--shape", default="",
-                    help="block,tpt,chunk: fixed launch shape instead of autotuning (profiling runs)")
+                    help="block,tpt,chunk[,slot_range]: fixed launch shape instead of autotuning "
+                         "(profiling runs)")
     return ap.parse_args()
 
 
@@ -474,8 +475,9 @@ def main():
         if mode not in tuned:  # launch-shape autotuning is part of the untimed warm-up
             cfg = g.Config(batch.n_phase, batch.n_mag, mode, t0=batch.t0, overlap=ovl)
             if args.shape:
-                b_, t_, c_ = (int(x) for x in args.shape.split(","))
-                g.gce_set_tuning(h, cfg, int(batch.n_obs.max()), block=b_, tpt=t_, chunk=c_)
+                sh = [int(x) for x in args.shape.split(",")]
+                g.gce_set_tuning(h, cfg, int(batch.n_obs.max()), block=sh[0], tpt=sh[1], chunk=sh[2],
+                                 slot_range=sh[3] if len(sh) > 3 else 0)
             else:  # tuned on a bounded slice of this very job
                 g.gce_autotune_job(h, t_d, m_d, offs, p_d, q_d, cfg)
             tuned[mode] = g.gce_get_tuning(h, cfg, int(batch.n_obs.max()), int(batch.pdots.size))

@@ -100,12 +100,19 @@ typedef struct {
  * or 512); tpt: trials per thread (1, 2, or 4 except with GCE_PHASE_FP64);
  * ctas_per_sm: resident CTAs per SM
  * (0 = as many as fit); chunk: light-curve points staged in shared memory at
- * once (a multiple of 256, 256 .. 8192). */
+ * once (a multiple of 256, 256 .. 8192); slot_range (GCE_PHASE_SPLIT32 jobs
+ * without a Pdot axis; ignored otherwise): 0 keeps a counter for every phase
+ * slot a fold can reach within the job's cycle limit, 1 keeps about a quarter
+ * fewer (fold residuals up to 9/16 cycle) and re-reduces the folds of every
+ * warp of trials whose cycles, |t - t0| f, could exceed that (about 5e5
+ * cycles): less shared memory per trial for the same counts, at three more
+ * FP32 operations per point where the re-reduction runs. */
 typedef struct {
     int32_t block;
     int32_t tpt;
     int32_t ctas_per_sm;
     int32_t chunk;
+    int32_t slot_range;
 } gce_tuning;
 
 typedef struct gce_handle_s *gce_handle;

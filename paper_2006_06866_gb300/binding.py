@@ -40,7 +40,8 @@ class gce_config(ctypes.Structure):
 
 class gce_tuning(ctypes.Structure):
     _fields_ = [("block", ctypes.c_int32), ("tpt", ctypes.c_int32),
-                ("ctas_per_sm", ctypes.c_int32), ("chunk", ctypes.c_int32)]
+                ("ctas_per_sm", ctypes.c_int32), ("chunk", ctypes.c_int32),
+                ("slot_range", ctypes.c_int32)]
 
 
 _P = ctypes.c_void_p
@@ -445,12 +446,13 @@ def gce_get_tuning(handle: Handle, cfg: Config, n_obs_hint: int, n_pdots: int = 
     t = gce_tuning()
     _check(lib().gce_get_tuning(handle.ptr, ctypes.byref(c), int(n_obs_hint), int(n_pdots),
                                 ctypes.byref(t)), handle.ptr)
-    return {"block": t.block, "tpt": t.tpt, "ctas_per_sm": t.ctas_per_sm, "chunk": t.chunk}
+    return {"block": t.block, "tpt": t.tpt, "ctas_per_sm": t.ctas_per_sm, "chunk": t.chunk,
+            "slot_range": t.slot_range}
 
 
 def gce_set_tuning(handle: Handle, cfg: Config, n_obs_hint: int, block=256, tpt=2,
-                   ctas_per_sm=0, chunk=2048):
+                   ctas_per_sm=0, chunk=2048, slot_range=0):
     c = cfg.c()
-    t = gce_tuning(int(block), int(tpt), int(ctas_per_sm), int(chunk))
+    t = gce_tuning(int(block), int(tpt), int(ctas_per_sm), int(chunk), int(slot_range))
     _check(lib().gce_set_tuning(handle.ptr, ctypes.byref(c), int(n_obs_hint), ctypes.byref(t)),
            handle.ptr)

@@ -167,6 +167,7 @@ static gce_tuning default_tuning(int mode, int n_max) {
     t.tpt = 2;
     t.ctas_per_sm = 0;
     t.chunk = mode == GCE_PHASE_FP64 ? 4096 : 2048;
+    t.slot_range = 0;
     (void)n_max;
     return t;
 }
@@ -175,7 +176,8 @@ static bool tuning_ok(const gce_tuning &t, int mode) {
     const bool block_ok = t.block == 64 || t.block == 128 || t.block == 256 || t.block == 512;
     const bool tpt_ok = t.tpt == 1 || t.tpt == 2 || (t.tpt == 4 && mode != GCE_PHASE_FP64);
     return block_ok && tpt_ok && t.ctas_per_sm >= 0 && t.ctas_per_sm <= 32 &&
-           t.chunk >= 256 && t.chunk <= 8192 && t.chunk % 256 == 0;
+           t.chunk >= 256 && t.chunk <= 8192 && t.chunk % 256 == 0 &&
+           (t.slot_range == 0 || t.slot_range == 1);
 }
 
 static TuneKey tune_key(const gce_config *cfg, int n_obs, int pd_axis) {
@@ -311,7 +313,7 @@ struct Plan {
     long long n_points, n_trials, n_items, n_long_items;
     long long n_lists;    // top-k candidate lists (and moment records) per curve: tiles x warps
     int n_long, n_short;  // curves taken curve-major / tile-major (see MainArgs)
-    int n_max, n_tiles, n_ptiles, pd_major, narrow, half, kv, block, tpt, grid, chunk, table_smem,
+    int n_max, n_tiles, n_ptiles, pd_major, range, half, kv, block, tpt, grid, chunk, table_smem,
         grab;
     int n_groups, tiles_per_group;  // top-k: first merge level (0 groups: none)
     size_t smem;
@@ -329,15 +331,18 @@ gce_status make_plan(gce_handle h, const Job &j, Plan &pl) {
     pl.n_max = (int)nmax;
     const gce_tuning t = j.force ? *j.force : lookup_tuning(h, cfg, pl.n_max, j.n_pdots > 1 ? 1 : 0);
     const int kk = j.kind == JOB_TOPK ? j.k : 0;
-    // a Pdot axis: SPLIT32 keeps the narrow slot range (every fold re-reduced)
-    pl.narrow = (cfg->phase_mode == GCE_PHASE_SPLIT32 && j.n_pdots > 1) ? 1 : 0;
+    // SPLIT32's kept slot range: narrow with a Pdot axis (every fold re-reduced),
+    // else the tuned one (mid: warps with many cycles re-reduce)
+    pl.range = RANGE_WIDE;
+    if (cfg->phase_mode == GCE_PHASE_SPLIT32)
+        pl.range = j.n_pdots > 1 ? RANGE_NARROW : t.slot_range == 1 ? RANGE_MID : RANGE_WIDE;
     // one Pdot value: the SPLIT32 / FIXED32 staging holds 8-byte half points
     pl.half = (cfg->phase_mode != GCE_PHASE_FP64 && j.n_pdots == 1) ? 1 : 0;
     // the kernel instantiation: overlapping bins or not
     pl.kv = kernel_variant((cfg->flags & GCE_FLAG_OVERLAP) != 0);
     const int kv = pl.kv;
     const ShapeKey skey(cfg->phase_mode, cfg->n_phase_bins, cfg->n_mag_bins, pl.n_max, kk,
-                        pl.narrow * 8 + pl.half * 4 + kv, t.block, t.tpt, t.chunk,
+                        pl.range * 8 + pl.half * 4 + kv, t.block, t.tpt, t.chunk,
                         t.ctas_per_sm);
     int occ = 0;
     auto sit = h->shapes.find(skey);
@@ -361,7 +366,7 @@ gce_status make_plan(gce_handle h, const Job &j, Plan &pl) {
         // block, until the CTA fits in shared memory
         auto size = [&]() {
             return main_smem_bytes(cfg->phase_mode, pl.block, pl.tpt, pl.chunk, cfg->n_phase_bins,
-                                   cfg->n_mag_bins, pl.table_smem, pl.narrow, pl.half);
+                                   cfg->n_mag_bins, pl.table_smem, pl.range, pl.half);
         };
         auto limit = [&]() {
             return main_dynamic_smem_limit(cfg->phase_mode, pl.tpt, pl.block, kv, (size_t)h->smem_optin);
@@ -498,7 +503,7 @@ gce_status enqueue(gce_handle h, const Job &j, const Plan &pl, cudaStream_t s, b
     ma.n_tiles = pl.n_tiles;
     ma.n_ptiles = pl.n_ptiles;
     ma.pd_major = pl.pd_major;
-    ma.narrow = pl.narrow;
+    ma.range = pl.range;
     ma.n_items = pl.n_items;
     ma.n_long_items = pl.n_long_items;
     ma.n_long = pl.n_long;
@@ -958,8 +963,9 @@ extern "C" gce_status gce_set_tuning(gce_handle h, const gce_config *cfg, int32_
     return GCE_OK;
 }
 
-// Candidate launch shapes of the autotuners.
-static std::vector<gce_tuning> tune_candidates(int mode, int n_obs) {
+// Candidate launch shapes of the autotuners (slot_range: the kept SPLIT32 slot
+// range of every candidate).
+static std::vector<gce_tuning> tune_candidates(int mode, int n_obs, int slot_range = 0) {
     const int blocks[] = {128, 256, 512};
     const int tpts[] = {1, 2, 4};
     const int chunks[] = {256, 512, 1024, 2048};
@@ -973,6 +979,7 @@ static std::vector<gce_tuning> tune_candidates(int mode, int n_obs) {
                 c.block = b;
                 c.tpt = tp;
                 c.chunk = ch;
+                c.slot_range = slot_range;
                 cands.push_back(c);
             }
     return cands;
@@ -981,10 +988,12 @@ static std::vector<gce_tuning> tune_candidates(int mode, int n_obs) {
 // Times every candidate on job j (one untimed run, then three timed ones), then
 // times the three fastest again over six runs each and leaves the fastest of
 // those in *best (a second look keeps close calls from being decided by one
-// noisy measurement); shapes that do not fit are skipped.
+// noisy measurement); shapes that do not fit are skipped.  also_wide: each of
+// the three is timed with the wide slot range too (the candidates keep the mid
+// one, whose re-reduced warps can make it the slower on long baselines).
 static gce_status time_candidates(gce_handle h, Job j, const std::vector<gce_tuning> &cands,
                                   cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1,
-                                  gce_tuning *best) {
+                                  gce_tuning *best, bool also_wide = false) {
     auto timed = [&](const gce_tuning &cand, int reps, float *ms) -> gce_status {
         j.force = &cand;
         *ms = 1e30f;
@@ -1008,11 +1017,15 @@ static gce_status time_candidates(gce_handle h, Job j, const std::vector<gce_tun
     std::sort(first.begin(), first.end());
     float best_ms = 1e30f;
     for (size_t r = 0; r < std::min<size_t>(3, first.size()); ++r) {
-        float ms;
-        if (gce_status st = timed(cands[first[r].second], 6, &ms)) return st;
-        if (ms < best_ms) {
-            best_ms = ms;
-            *best = cands[first[r].second];
+        for (int w = 0; w < (also_wide ? 2 : 1); ++w) {
+            gce_tuning c = cands[first[r].second];
+            if (w) c.slot_range = 0;
+            float ms;
+            if (gce_status st = timed(c, 6, &ms)) return st;
+            if (ms < best_ms) {
+                best_ms = ms;
+                *best = c;
+            }
         }
     }
     return GCE_OK;
@@ -1071,7 +1084,11 @@ extern "C" gce_status gce_autotune_job(gce_handle h, const double *times, const 
         j.times = times; j.mags = mags; j.h_offsets = h_offsets; j.n_curves = c2;
         j.periods = d_p; j.n_periods = n_p2; j.pdots = d_q; j.n_pdots = n_q2;
         j.cfg = &c2cfg; j.k = 1; j.topk_H = d_H; j.topk_idx = d_I;
-        result = time_candidates(h, j, tune_candidates(cfg->phase_mode, (int)nmax), s, e0, e1, &best);
+        // SPLIT32 without a Pdot axis: candidates with the mid slot range, the
+        // finalists with the wide one as well
+        const bool mid = cfg->phase_mode == GCE_PHASE_SPLIT32 && n_pdots == 1;
+        result = time_candidates(h, j, tune_candidates(cfg->phase_mode, (int)nmax, mid ? 1 : 0), s,
+                                 e0, e1, &best, mid);
     } while (0);
     if (s) cudaStreamSynchronize(s);
     if (e0) cudaEventDestroy(e0);

@@ -162,8 +162,8 @@ __device__ __forceinline__ float fold_split_fpart(float4 pt, float4 tr) {
 
 // The rest of the fold from the period part c: the Pdot term -a tau^2 reduced
 // the same way, the sum reduced once more, then the slot.  REDUCE (without
-// Pdot): the residual is reduced once more as well, to |x| <= 1/2, for jobs that
-// keep only the narrow slot range.
+// Pdot): the residual is reduced once more as well, to |x| <= 1/2, for folds that
+// must stay in the narrow slot range (see slot_range).
 template <bool PDOT, bool REDUCE = false>
 __device__ __forceinline__ int fold_split_from(float c, float4 pt, float4 tr, float nphi,
                                                float zoff) {
@@ -286,26 +286,33 @@ __device__ __forceinline__ unsigned int fold_fixed_bin_from(unsigned int acc, ui
 // The counter slots a trial keeps: logical slots [zmin, zmax] (fine phase
 // bins; 50 %-overlapping bins are formed from them in the epilogue).  FP64 and
 // FIXED32 count phase bins directly.  SPLIT32's slot is floor(x n + n) for the
-// fold residual x; a job that passes the range check (cycles < 2^21) has |x| <=
-// 3/4 + 2^-20 (r within 1/2, each cross term within 2^-24 |th fh| < 1/8, three
-// roundings), so slots outside [floor(n (1/4 - 2^-16)), floor(n (7/4 + 2^-16))]
-// are never reached.  narrow: every fold of the job re-reduces its residual to
-// |x| <= 1/2 (jobs with a Pdot axis, whose folds do that anyway), and only
-// [floor(n (1/2 - 2^-16)), floor(n (3/2 + 2^-16))] is kept.
+// fold residual x, and the kept range is set by a bound on |x|:
+//   RANGE_WIDE: a job that passes the range check (cycles < 2^21) has |x| <=
+//     3/4 + 2^-20 (r within 1/2, each cross term within 2^-24 |th fh| < 1/8,
+//     three roundings), so slots outside [floor(n (1/4 - 2^-16)),
+//     floor(n (7/4 + 2^-16))] are never reached;
+//   RANGE_NARROW: every fold of the job re-reduces its residual to |x| <= 1/2
+//     (jobs with a Pdot axis, whose folds do that anyway), and only
+//     [floor(n (1/2 - 2^-16)), floor(n (3/2 + 2^-16))] is kept;
+//   RANGE_MID: |x| <= 9/16 + 2^-16 is kept; a warp whose trials could fold
+//     outside it (the bound of split_slot_window) re-reduces its folds as in
+//     RANGE_NARROW, the others fold as in RANGE_WIDE.
+enum { RANGE_WIDE = 0, RANGE_NARROW = 1, RANGE_MID = 2 };
 struct SlotRange {
     int zmin, zmax;
 };
-__host__ __device__ inline SlotRange slot_range(int mode, int n_phase, bool narrow) {
+__host__ __device__ inline SlotRange slot_range(int mode, int n_phase, int range) {
     if (mode != GCE_PHASE_SPLIT32) return {0, n_phase - 1};
-    const double xw = (narrow ? 0.5 : 0.75) + 1.0 / 65536.0;
+    const double xw =
+        (range == RANGE_NARROW ? 0.5 : range == RANGE_MID ? 0.5625 : 0.75) + 1.0 / 65536.0;
     int zmin = (int)floor((double)n_phase * (1.0 - xw));
     int zmax = (int)floor((double)n_phase * (1.0 + xw));
     if (zmin < 0) zmin = 0;
     if (zmax > 2 * n_phase - 1) zmax = 2 * n_phase - 1;
     return {zmin, zmax};
 }
-__host__ __device__ inline int slots_per_trial(int mode, int n_phase, bool narrow) {
-    const SlotRange r = slot_range(mode, n_phase, narrow);
+__host__ __device__ inline int slots_per_trial(int mode, int n_phase, int range) {
+    const SlotRange r = slot_range(mode, n_phase, range);
     return r.zmax - r.zmin + 1;
 }
 
@@ -321,12 +328,12 @@ struct MainSmemLayout {
 };
 __host__ __device__ inline MainSmemLayout main_smem_layout(int mode, int block, int tpt, int chunk,
                                                            int n_phase, int n_mag,
-                                                           int table_smem, int narrow, int half) {
+                                                           int table_smem, int range, int half) {
     MainSmemLayout L;
     const unsigned int pt = (mode == GCE_PHASE_FP64 || half) ? 8u : 16u;
     L.pts = 8u * (unsigned int)((table_smem + 1) & ~1);
     L.cnt = L.pts + pt * (unsigned int)chunk;
-    L.seg = L.cnt + 4u * (unsigned int)(tpt * slots_per_trial(mode, n_phase, narrow != 0) * block);
+    L.seg = L.cnt + 4u * (unsigned int)(tpt * slots_per_trial(mode, n_phase, range) * block);
     L.total = L.seg + 4u * (unsigned int)(n_mag + 1);
     return L;
 }
@@ -404,7 +411,7 @@ struct MainArgs {
     int n_tiles;               // trial tiles per curve
     int n_ptiles;              // period-major tiling: tiles along the periods
     int pd_major;              // tile = block periods x tpt Pdot values (else flat runs)
-    int narrow;                // SPLIT32: narrow slot range, every fold re-reduced
+    int range;                 // SPLIT32: the kept slot range (RANGE_*)
     long long n_items;         // n_curves * n_tiles
     // items [0, n_long_items) are (curve, tile) pairs of the first n_long curves
     // of `order`, curve-major; the rest pair the n_short curves after them with
@@ -447,7 +454,7 @@ cudaError_t launch_band_stats(const double *mags, const unsigned char *bands,
                               double2 *stats, JobState *st, cudaStream_t s);
 cudaError_t launch_table(unsigned long long *table, int n_max, cudaStream_t s);
 size_t main_smem_bytes(int mode, int block, int tpt, int chunk, int n_phase, int n_mag,
-                       int table_smem, int narrow, int half);
+                       int table_smem, int range, int half);
 size_t single_smem_bytes(int n_phase, int block);
 size_t main_dynamic_smem_limit(int mode, int tpt, int block, int kv, size_t smem_optin);
 cudaError_t main_kernel_attrs(int mode, int tpt, int block, int kv, size_t smem_optin);

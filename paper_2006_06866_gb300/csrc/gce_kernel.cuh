@@ -118,7 +118,7 @@ template <> struct Fold<GCE_PHASE_SPLIT32> {
     __device__ __forceinline__ static fpart_t fpart(float4 p, const prep_t &t) {
         return fold_split_fpart(p, t);
     }
-    // RED: re-reduce the residual without Pdot as well (narrow slot range)
+    // RED: re-reduce the residual without Pdot as well (narrow slot window)
     template <bool PDOT, bool K0, int SH, bool RED>
     __device__ __forceinline__ static unsigned int offset_from(fpart_t f, float4 p,
                                                                const prep_t &t,
@@ -172,15 +172,57 @@ __device__ __forceinline__ void red_shared_add(unsigned int addr, unsigned int i
 }
 __device__ __forceinline__ void compiler_fence() { asm volatile("" ::: "memory"); }
 
-// The hot loop: every point of [ka, kb) (shared memory, broadcast) folded for
-// the thread's TPT trials and counted into the thread's private counters.
-// base[s]: shared-memory address of trial s's logical slot 0 minus the mode's
-// slot bias (mod 2^32); a slot's word is base + (raw << SH), SH = log2(4 block).
-// Each point counts once, in its fine phase bin, also with 50 %-overlapping
-// bins (their counts are sums of adjacent fine bins, formed in the epilogue).
-// SHARED: the thread's trials share their period (period-major tiles), so the
-// fold's period part is computed once per point for all of them.
-// HALF: the staged points are half points (no Pdot term anywhere in the job).
+// One point folded for the thread's TPT trials and counted into their private
+// counters.  base[s]: shared-memory address of trial s's logical slot 0 minus
+// the mode's slot bias (mod 2^32); a slot's word is base + (raw << SH), SH =
+// log2(4 block).  Each point counts once, in its fine phase bin, also with
+// 50 %-overlapping bins (their counts are sums of adjacent fine bins, formed in
+// the epilogue).  SHARED: the thread's trials share their period (period-major
+// tiles), so the fold's period part is computed once for all of them.
+template <int MODE, int TPT, int SH, bool PDOT, bool K0, bool RED, bool SHARED>
+__device__ __forceinline__ void count_point(const typename ModeTraits<MODE>::point_t &p,
+                                            const typename Fold<MODE>::prep_t (&tc)[TPT],
+                                            const unsigned int (&base)[TPT], const FoldConst &fk,
+                                            unsigned int inc) {
+    typename Fold<MODE>::fpart_t fp{};
+    if (SHARED) fp = Fold<MODE>::fpart(p, tc[0]);
+#pragma unroll
+    for (int s = 0; s < TPT; ++s) {
+        const unsigned int addr =
+            base[s] + (SHARED ? Fold<MODE>::template offset_from<PDOT, K0, SH, RED>(fp, p, tc[s], fk)
+                              : Fold<MODE>::template offset<PDOT, K0, SH, RED>(p, tc[s], fk));
+#if defined(GCE_CHECK_SLOTS)
+        // checked builds: the logical slot of this increment must lie in the
+        // kept range; a miss is flagged and the access skipped
+        const int lslot =
+            (int)(addr - (base[s] + ((unsigned int)Fold<MODE>::kSlotBias << SH))) >> SH;
+        if (lslot < fk.zmin || lslot > fk.zmax) {
+            atomicOr(fk.err, (unsigned int)ERR_SLOT);
+            continue;
+        }
+#endif
+        red_shared_add(addr, inc);
+    }
+}
+
+// Two half points from one 16-byte word.
+__device__ __forceinline__ void split_pair(const float4 &q, float2 &a, float2 &b) {
+    a = make_float2(q.x, q.y);
+    b = make_float2(q.z, q.w);
+}
+__device__ __forceinline__ void split_pair(const uint4 &q, uint2 &a, uint2 &b) {
+    a = make_uint2(q.x, q.y);
+    b = make_uint2(q.z, q.w);
+}
+template <class H> struct PairOf;
+template <> struct PairOf<float2> { typedef float4 type; };
+template <> struct PairOf<uint2> { typedef uint4 type; };
+
+// The hot loop: every point of [ka, kb) (shared memory, broadcast) through
+// count_point.  HALF: the staged points are half points (no Pdot term anywhere
+// in the job); PAIRS below reads them two per 16-byte shared load (the chunk
+// starts 16-byte aligned; a segment starting at an odd index takes its first
+// point alone).
 template <int MODE, int TPT, int SH, bool PDOT, bool K0, bool RED, bool SHARED, bool HALF>
 __device__ __forceinline__ void count_points(
     const void *__restrict__ pts, int ka, int kb,
@@ -191,29 +233,37 @@ __device__ __forceinline__ void count_points(
     // points unrolled by 16 (8 with the longer Pdot fold): measured faster than 8
     // and 4 on every workload without a Pdot axis, and than 16 with one
     constexpr int UNROLL = PDOT ? 8 : 16;
+    // pairs measured faster with one trial per thread (+20 % at 50 overlapping
+    // bins, where one point load serves one trial) and with FIXED32 (+5 % at
+    // four trials), slower with SPLIT32 at two or four trials (-5 %, -1 %)
+    constexpr bool PAIRS = HALF && (TPT == 1 || MODE == GCE_PHASE_FIXED32);
+    if constexpr (PAIRS) {
+        typedef typename MT::half_t half_t;
+        typedef typename PairOf<half_t>::type pair_t;
+        const half_t *hp = static_cast<const half_t *>(pts);
+        int k = ka;
+        if ((k & 1) && k < kb) {
+            count_point<MODE, TPT, SH, PDOT, K0, RED, SHARED>(MT::widen(hp[k]), tc, base, fk, inc);
+            ++k;
+        }
+        constexpr int UNROLL2 = UNROLL / 2;
+#pragma unroll UNROLL2
+        for (; k + 1 < kb; k += 2) {
+            const pair_t q = *reinterpret_cast<const pair_t *>(hp + k);
+            half_t h0, h1;
+            split_pair(q, h0, h1);
+            count_point<MODE, TPT, SH, PDOT, K0, RED, SHARED>(MT::widen(h0), tc, base, fk, inc);
+            count_point<MODE, TPT, SH, PDOT, K0, RED, SHARED>(MT::widen(h1), tc, base, fk, inc);
+        }
+        if (k < kb)
+            count_point<MODE, TPT, SH, PDOT, K0, RED, SHARED>(MT::widen(hp[k]), tc, base, fk, inc);
+    } else {
 #pragma unroll UNROLL
-    for (int k = ka; k < kb; ++k) {
-        const typename MT::point_t p =
-            HALF ? MT::widen(static_cast<const typename MT::half_t *>(pts)[k])
-                 : static_cast<const typename MT::point_t *>(pts)[k];
-        typename Fold<MODE>::fpart_t fp{};
-        if (SHARED) fp = Fold<MODE>::fpart(p, tc[0]);
-#pragma unroll
-        for (int s = 0; s < TPT; ++s) {
-            const unsigned int addr =
-                base[s] + (SHARED ? Fold<MODE>::template offset_from<PDOT, K0, SH, RED>(fp, p, tc[s], fk)
-                                  : Fold<MODE>::template offset<PDOT, K0, SH, RED>(p, tc[s], fk));
-#if defined(GCE_CHECK_SLOTS)
-            // checked builds: the logical slot of this increment must lie in the
-            // kept range; a miss is flagged and the access skipped
-            const int lslot =
-                (int)(addr - (base[s] + ((unsigned int)Fold<MODE>::kSlotBias << SH))) >> SH;
-            if (lslot < fk.zmin || lslot > fk.zmax) {
-                atomicOr(fk.err, (unsigned int)ERR_SLOT);
-                continue;
-            }
-#endif
-            red_shared_add(addr, inc);
+        for (int k = ka; k < kb; ++k) {
+            const typename MT::point_t p =
+                HALF ? MT::widen(static_cast<const typename MT::half_t *>(pts)[k])
+                     : static_cast<const typename MT::point_t *>(pts)[k];
+            count_point<MODE, TPT, SH, PDOT, K0, RED, SHARED>(p, tc, base, fk, inc);
         }
     }
 }
@@ -529,16 +579,16 @@ __global__ void __launch_bounds__(1 << LOG2B, main_min_blocks(TPT, LOG2B)) k_mai
     const int n_phase = a.n_phase, n_mag = a.n_mag;
     constexpr bool SPLIT = MODE == GCE_PHASE_SPLIT32;
     constexpr int ovl = OVL ? 1 : 0;  // 50 %-overlapping phase bins
-    const bool narrow = SPLIT && a.narrow != 0;
-    const SlotRange zr = slot_range(MODE, n_phase, narrow);
-    const int n_slots = slots_per_trial(MODE, n_phase, narrow);
+    const int range = SPLIT ? a.range : (int)RANGE_WIDE;
+    const SlotRange zr = slot_range(MODE, n_phase, range);
+    const int n_slots = slots_per_trial(MODE, n_phase, range);
     const int slot_off = -zr.zmin;  // physical index of logical slot l: l + slot_off
     const int stride_j = B, stride_s = n_slots * B;
 
     // the regions at the offsets the host sized the launch with (the table first,
     // so that its address is a constant)
     const MainSmemLayout lay = main_smem_layout(MODE, B, TPT, a.chunk, n_phase, n_mag, a.table_smem,
-                                                narrow ? 1 : 0, a.half);
+                                                range, a.half);
     unsigned long long *s_tab = reinterpret_cast<unsigned long long *>(smem);
     point_t *s_pts = reinterpret_cast<point_t *>(smem + lay.pts);
     unsigned int *s_cnt = reinterpret_cast<unsigned int *>(smem + lay.cnt);
@@ -584,6 +634,7 @@ __global__ void __launch_bounds__(1 << LOG2B, main_min_blocks(TPT, LOG2B)) k_mai
     typename Fold<MODE>::prep_t tc[TPT];
     long long tt[TPT];
     bool pdot = false, k0 = true;
+    bool red = false;  // SPLIT32: this warp's folds re-reduce the residual (narrow window)
     const bool pdm = a.pd_major != 0;
     int wl[TPT];           // word offset (from my_cnt) of each trial's first window slot
 
@@ -659,8 +710,16 @@ __global__ void __launch_bounds__(1 << LOG2B, main_min_blocks(TPT, LOG2B)) k_mai
                 for (int s = 0; s < TPT; ++s)
                     if (tt[s] < a.n_trials) fm = fmaxf(fm, fabsf(split_fh(tc[s])));
                 fm = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(fm)));
+                // folds without a Pdot term re-reduce their residual with the
+                // narrow range, and with the mid one where the warp's cycles
+                // could fold outside it (a fold with a Pdot term always does)
+                red = !pdot && range == RANGE_NARROW;
                 int zlo, zhi;
-                split_slot_window(pdot || narrow, tau_max_f * fm, n_phase, zlo, zhi);
+                split_slot_window(pdot || red, tau_max_f * fm, n_phase, zlo, zhi);
+                if (!pdot && range == RANGE_MID && (zlo < zr.zmin || zhi > zr.zmax)) {
+                    red = true;
+                    split_slot_window(true, tau_max_f * fm, n_phase, zlo, zhi);
+                }
                 L = max(zlo, zr.zmin);
                 R = min(zhi, zr.zmax);
             }
@@ -718,8 +777,11 @@ __global__ void __launch_bounds__(1 << LOG2B, main_min_blocks(TPT, LOG2B)) k_mai
                     constexpr bool HP = MODE != GCE_PHASE_FP64;  // half points exist
                     if (k0) {
                         if (pdot) count_points_any<MODE, TPT, SH, true, true>(pdm, pp, ka - lo, kb - lo, tc, base, fk, inc);
+                        // (red: the warp's slot window is the narrow one, so its folds
+                        // must re-reduce, with half points as with whole ones)
+                        else if (SPLIT && red && half) count_points_any<MODE, TPT, SH, false, true, SPLIT, HP>(pdm, pp, ka - lo, kb - lo, tc, base, fk, inc);
+                        else if (SPLIT && red) count_points_any<MODE, TPT, SH, false, true, SPLIT>(pdm, pp, ka - lo, kb - lo, tc, base, fk, inc);
                         else if (HP && half) count_points_any<MODE, TPT, SH, false, true, false, HP>(pdm, pp, ka - lo, kb - lo, tc, base, fk, inc);
-                        else if (SPLIT && narrow) count_points_any<MODE, TPT, SH, false, true, SPLIT>(pdm, pp, ka - lo, kb - lo, tc, base, fk, inc);
                         else count_points_any<MODE, TPT, SH, false, true>(pdm, pp, ka - lo, kb - lo, tc, base, fk, inc);
                     } else if (MODE == GCE_PHASE_FIXED32) {
                         if (pdot) count_points_any<MODE, TPT, SH, true, false>(pdm, pp, ka - lo, kb - lo, tc, base, fk, inc);

@@ -141,8 +141,8 @@ __global__ void k_counts(MainArgs a, long long n_cells, const long long *cell_cu
 }  // namespace
 
 size_t main_smem_bytes(int mode, int block, int tpt, int chunk, int n_phase, int n_mag,
-                       int table_smem, int narrow, int half) {
-    return main_smem_layout(mode, block, tpt, chunk, n_phase, n_mag, table_smem, narrow, half).total;
+                       int table_smem, int range, int half) {
+    return main_smem_layout(mode, block, tpt, chunk, n_phase, n_mag, table_smem, range, half).total;
 }
 
 size_t single_smem_bytes(int n_phase, int block) { return 4 * (size_t)n_phase * block; }

@@ -167,10 +167,10 @@ extern "C" gce_status gce_ce_topk_static(const double *times, const double *mags
     int chunk = (int)((n_max + 31) / 32 * 32);
     if (chunk > 1024) chunk = 1024;
     int table_smem = (int)(n_max + 1 < 1024 ? n_max + 1 : 1024);
-    const int narrow = (mode == GCE_PHASE_SPLIT32 && n_pdots > 1) ? 1 : 0;
+    const int range = (mode == GCE_PHASE_SPLIT32 && n_pdots > 1) ? RANGE_NARROW : RANGE_WIDE;
     const int half = (mode != GCE_PHASE_FP64 && n_pdots == 1) ? 1 : 0;
     const size_t smem = main_smem_bytes(mode, block, tpt, chunk, cfg->n_phase_bins,
-                                        cfg->n_mag_bins, table_smem, narrow, half);
+                                        cfg->n_mag_bins, table_smem, range, half);
     const int kv = kernel_variant((cfg->flags & GCE_FLAG_OVERLAP) != 0);
     if (smem > main_dynamic_smem_limit(mode, tpt, block, kv, (size_t)d->smem_optin))
         return fail(GCE_ERR_UNSUPPORTED, "bin counts too large for this entry point");
@@ -238,7 +238,7 @@ extern "C" gce_status gce_ce_topk_static(const double *times, const double *mags
     ma.n_tiles = (int)n_tiles;
     ma.n_ptiles = tg.n_ptiles;
     ma.pd_major = tg.pd_major;
-    ma.narrow = narrow;
+    ma.range = range;
     ma.n_items = n_items;
     ma.n_long_items = n_items;  // every curve curve-major
     ma.n_long = n_curves;

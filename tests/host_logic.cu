@@ -73,31 +73,43 @@ static void check_topk_groups(std::mt19937_64 &rng) {
 }
 
 // SPLIT32 slots: the fold's residual x satisfies |x| <= 3/4 + 2^-20 under the
-// job's range check (|x| <= 1/2 + 2^-20 where every fold re-reduces it), and
-// the slot of x is floor(n x + n); the kept range must hold every such slot and
-// stay within the 2n slots of a trial.  The other folds keep the n phase bins.
+// job's range check (|x| <= 1/2 + 2^-20 where a fold re-reduces it; the mid
+// range is used by folds whose warp's bound is within 9/16, the others
+// re-reduce), and the slot of x is floor(n x + n); the kept range must hold
+// every such slot and stay within the 2n slots of a trial, and the mid range
+// must lie between the narrow and the wide one.  The other folds keep the n
+// phase bins.
 static void check_slot_range() {
     for (int n = 1; n <= GCE_MAX_PHASE_BINS; ++n) {
-        for (int narrow = 0; narrow < 2; ++narrow) {
-            const double xb = (narrow ? 0.5 : 0.75) + std::ldexp(1.0, -20);
-            const SlotRange r = slot_range(GCE_PHASE_SPLIT32, n, narrow != 0);
+        for (int range : {RANGE_WIDE, RANGE_NARROW, RANGE_MID}) {
+            const double xb = (range == RANGE_NARROW ? 0.5 : range == RANGE_MID ? 0.5625 : 0.75) +
+                              std::ldexp(1.0, -20);
+            const SlotRange r = slot_range(GCE_PHASE_SPLIT32, n, range);
             const int lo = (int)std::floor(-xb * n + n), hi = (int)std::floor(xb * n + n);
             CHECK(r.zmin <= std::max(lo, 0) && r.zmax >= std::min(hi, 2 * n - 1),
-                  "n %d narrow %d: kept [%d, %d], reachable [%d, %d]", n, narrow, r.zmin, r.zmax,
+                  "n %d range %d: kept [%d, %d], reachable [%d, %d]", n, range, r.zmin, r.zmax,
                   lo, hi);
             CHECK(r.zmin >= 0 && r.zmax <= 2 * n - 1 && r.zmin <= r.zmax,
-                  "n %d narrow %d: [%d, %d] outside [0, 2n)", n, narrow, r.zmin, r.zmax);
-            CHECK(slots_per_trial(GCE_PHASE_SPLIT32, n, narrow != 0) == r.zmax - r.zmin + 1,
+                  "n %d range %d: [%d, %d] outside [0, 2n)", n, range, r.zmin, r.zmax);
+            CHECK(slots_per_trial(GCE_PHASE_SPLIT32, n, range) == r.zmax - r.zmin + 1,
                   "n %d: slots per trial", n);
             // every phase bin keeps at least one of its two slots (j and j + n)
             for (int j = 0; j < n; ++j)
                 CHECK((j >= r.zmin && j <= r.zmax) || (j + n >= r.zmin && j + n <= r.zmax),
-                      "n %d narrow %d: bin %d has no slot", n, narrow, j);
+                      "n %d range %d: bin %d has no slot", n, range, j);
         }
+        const SlotRange w = slot_range(GCE_PHASE_SPLIT32, n, RANGE_WIDE);
+        const SlotRange m = slot_range(GCE_PHASE_SPLIT32, n, RANGE_MID);
+        const SlotRange q = slot_range(GCE_PHASE_SPLIT32, n, RANGE_NARROW);
+        CHECK(w.zmin <= m.zmin && m.zmin <= q.zmin && q.zmax <= m.zmax && m.zmax <= w.zmax,
+              "n %d: mid range [%d, %d] not between narrow [%d, %d] and wide [%d, %d]", n,
+              m.zmin, m.zmax, q.zmin, q.zmax, w.zmin, w.zmax);
         for (int mode : {GCE_PHASE_FP64, GCE_PHASE_FIXED32}) {
-            const SlotRange r = slot_range(mode, n, false);
-            CHECK(r.zmin == 0 && r.zmax == n - 1, "mode %d n %d: [%d, %d]", mode, n, r.zmin,
-                  r.zmax);
+            for (int range : {RANGE_WIDE, RANGE_NARROW, RANGE_MID}) {
+                const SlotRange r = slot_range(mode, n, range);
+                CHECK(r.zmin == 0 && r.zmax == n - 1, "mode %d n %d: [%d, %d]", mode, n, r.zmin,
+                      r.zmax);
+            }
         }
     }
 }
@@ -115,11 +127,11 @@ static void check_smem_layout(std::mt19937_64 &rng) {
         const int n_phase = 1 + (int)(rng() % GCE_MAX_PHASE_BINS);
         const int n_mag = 1 + (int)(rng() % GCE_MAX_MAG_BINS);
         const int table = 1 + (int)(rng() % 2048);
-        const int narrow = (int)(rng() % 2), half = (int)(rng() % 2);
+        const int range = (int)(rng() % 3), half = (int)(rng() % 2);
         const MainSmemLayout L =
-            main_smem_layout(mode, B, T, chunk, n_phase, n_mag, table, narrow, half);
+            main_smem_layout(mode, B, T, chunk, n_phase, n_mag, table, range, half);
         const unsigned int pt = (mode == GCE_PHASE_FP64 || half) ? 8u : 16u;
-        const unsigned int cnt = 4u * (unsigned int)(T * slots_per_trial(mode, n_phase, narrow != 0) * B);
+        const unsigned int cnt = 4u * (unsigned int)(T * slots_per_trial(mode, n_phase, range) * B);
         CHECK(L.pts >= 8u * (unsigned int)table && L.pts % 16 == 0, "pts %u table %d", L.pts, table);
         CHECK(L.cnt == L.pts + pt * (unsigned int)chunk && L.cnt % 16 == 0, "cnt %u", L.cnt);
         CHECK(L.seg == L.cnt + cnt && L.seg % 4 == 0, "seg %u", L.seg);

@@ -175,6 +175,38 @@ def test_split_narrow_slots_without_pdot(h, n_phase):
     compare_grid("split32", one.astype(np.float64), ref, dmin)
 
 
+@pytest.mark.parametrize("n_phase,overlap", [(2, False), (15, False), (50, False), (15, True),
+                                             (50, True)])
+def test_split_mid_slot_range(h, n_phase, overlap):
+    """SPLIT32's mid slot range (slot_range = 1) keeps fewer counter slots; the warps
+    whose trials could fold outside it (here the periods below about 400, a third of
+    the grid, at 2e8 time units) re-reduce their residuals, the others do not.  Either
+    way the counts are those of the wide range: the grids agree bit for bit at every
+    trials-per-thread, and with the oracle."""
+    rng = np.random.default_rng(47)
+    n_obs, n_curves = 300, 3
+    ts = [np.sort(rng.uniform(0.0, 2.0e8, n_obs)) for _ in range(n_curves)]
+    ms = [15 + 0.3 * np.sin(2 * np.pi * t / 731.3) + rng.normal(0, 0.05, n_obs) for t in ts]
+    offs = np.arange(n_curves + 1, dtype=np.int64) * n_obs
+    periods = np.geomspace(96.0, 5000.0, 257)
+    b = synth.LightCurveBatch("mid", np.concatenate(ts), np.concatenate(ms), offs, periods,
+                              np.zeros(1), n_phase, 10, np.zeros(n_curves), np.zeros(n_curves),
+                              np.zeros(n_curves))
+    cfg = g.Config(n_phase, 10, "split32", overlap=overlap)
+    grids = {}
+    for tpt in (1, 2, 4):
+        for sr in (0, 1):
+            g.gce_set_tuning(h, cfg, n_obs, block=128, tpt=tpt, chunk=512, slot_range=sr)
+            assert g.gce_get_tuning(h, cfg, n_obs)["slot_range"] == sr
+            grids[tpt, sr] = g.gce_ce_grid(h, cfg=cfg, **dev_args(b)).cpu().numpy()
+            assert g.gce_stream_status(h) == g.GCE_OK
+        assert np.array_equal(grids[tpt, 0], grids[tpt, 1])
+    g.gce_set_tuning(h, cfg, n_obs, block=256, tpt=2, chunk=2048)
+    ref, dmin = oracle.Oracle().ce_grid(b.times, b.mags, b.offsets, b.periods, b.pdots, n_phase,
+                                        10, with_dmin=True, overlap=overlap)
+    compare_grid("split32", grids[2, 1].astype(np.float64), ref, dmin)
+
+
 @pytest.mark.parametrize("mode", MODES)
 def test_longest_curve(h, mode):
     """A curve of the maximum length (65,535 points: counts above the 2048 c ln c entries
