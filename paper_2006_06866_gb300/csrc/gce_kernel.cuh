@@ -294,13 +294,17 @@ __device__ __forceinline__ int take_segment(unsigned int *w) {
 //     magnitude segment, so the segment's count is count - snapshot.
 //   FMT_PK2: (C << 20) | (B << 10) | A, for curves of at most kPk2MaxN points.
 //     Consecutive non-empty magnitude segments alternate between the fields A
-//     (increment 1) and B (increment 1 << 10); C is the cumulative count of the
-//     segments already swept.  One sweep then serves two segments: it reads A and
-//     B, adds them to C and clears them.
-// No field can overflow: each is at most the curve's point count.
+//     and B, and every point also counts in C, the cumulative count (the
+//     increment is 1 + 2^20 or 2^10 + 2^20: still one shared atomic).  One sweep
+//     then serves two segments: it reads A and B and clears them.
+// No field can overflow: each is at most the curve's point count.  Nor can the
+// field-wise sum of two words of different fine bins (the points are disjoint),
+// so with FMT_PK2 an overlapping bin's counts are read from the sum of its two
+// fine words (kPairWords).
 enum { FMT_SNAP = 0, FMT_PK2 = 1 };
 constexpr int kPk2MaxN = 1023;
 constexpr unsigned int kPk2IncB = 1u << 10;
+constexpr unsigned int kPk2IncC = 1u << 20;
 
 // Per counter word: the byte offsets 8 c into the c ln c table of the counts a
 // sweep reads, and the word it leaves behind.
@@ -313,10 +317,13 @@ enum { SW_SEG = 0, SW_LAST = 1 };
 //            count c_j (added: the Sigma_j T(c_j) term), the word cleared.
 // Fields<FMT, KIND>::get returns the byte offsets 8 c into the c ln c table of
 // the NF counts, and the word to store back; sign(f) says whether count f is
-// added (+1) or subtracted (-1).
+// added (+1) or subtracted (-1).  With kPairWords the offsets of a word (or of a
+// field-wise sum of words) and the word to store back are also available apart
+// (offsets, next).
 template <int FMT, int KIND> struct Fields;
 template <> struct Fields<FMT_SNAP, SW_SEG> {
     static constexpr int NF = 1;
+    static constexpr bool kPairWords = false;
     __device__ __forceinline__ static int sign(int) { return -1; }
     __device__ __forceinline__ static unsigned int get(unsigned int v, unsigned int (&o)[1]) {
         const unsigned int nv = __byte_perm(v, 0u, 0x1010);  // snapshot moved up
@@ -330,6 +337,7 @@ template <> struct Fields<FMT_SNAP, SW_SEG> {
 };
 template <> struct Fields<FMT_SNAP, SW_LAST> {
     static constexpr int NF = 2;
+    static constexpr bool kPairWords = false;
     __device__ __forceinline__ static int sign(int f) { return f == 0 ? -1 : 1; }
     __device__ __forceinline__ static unsigned int get(unsigned int v, unsigned int (&o)[2]) {
         o[0] = (__byte_perm(v, 0u, 0x1010) - v) >> 13;
@@ -340,26 +348,36 @@ template <> struct Fields<FMT_SNAP, SW_LAST> {
         return Fields<FMT_SNAP, SW_SEG>::merge(first, extra);
     }
 };
-template <> struct Fields<FMT_PK2, SW_SEG> {  // segments A and B; both added to C
+template <> struct Fields<FMT_PK2, SW_SEG> {  // segments A and B; both cleared
     static constexpr int NF = 2;
+    static constexpr bool kPairWords = true;
     __device__ __forceinline__ static int sign(int) { return -1; }
+    __device__ __forceinline__ static void offsets(unsigned int w, unsigned int (&o)[2]) {
+        o[0] = (w << 3) & 0x1ff8u;
+        o[1] = (w >> 7) & 0x1ff8u;
+    }
+    __device__ __forceinline__ static unsigned int next(unsigned int v) { return v & 0xfff00000u; }
     __device__ __forceinline__ static unsigned int get(unsigned int v, unsigned int (&o)[2]) {
-        o[0] = (v << 3) & 0x1ff8u;
-        o[1] = (v >> 7) & 0x1ff8u;
-        return (v & 0xfff00000u) + ((o[0] + o[1]) << 17);
+        offsets(v, o);
+        return next(v);
     }
     __device__ __forceinline__ static unsigned int merge(unsigned int first, unsigned int extra) {
         return first + extra;
     }
 };
-template <> struct Fields<FMT_PK2, SW_LAST> {  // A, B and C + A + B; word cleared
+template <> struct Fields<FMT_PK2, SW_LAST> {  // A, B and the cumulative C; word cleared
     static constexpr int NF = 3;
+    static constexpr bool kPairWords = true;
     __device__ __forceinline__ static int sign(int f) { return f == 2 ? 1 : -1; }
+    __device__ __forceinline__ static void offsets(unsigned int w, unsigned int (&o)[3]) {
+        o[0] = (w << 3) & 0x1ff8u;
+        o[1] = (w >> 7) & 0x1ff8u;
+        o[2] = (w >> 17) & 0x7ff8u;
+    }
+    __device__ __forceinline__ static unsigned int next(unsigned int) { return 0u; }
     __device__ __forceinline__ static unsigned int get(unsigned int v, unsigned int (&o)[3]) {
-        o[0] = (v << 3) & 0x1ff8u;
-        o[1] = (v >> 7) & 0x1ff8u;
-        o[2] = ((v >> 17) & 0x7ff8u) + o[0] + o[1];
-        return 0u;
+        offsets(v, o);
+        return next(v);
     }
     __device__ __forceinline__ static unsigned int merge(unsigned int first, unsigned int extra) {
         return first + extra;
@@ -390,6 +408,8 @@ struct Sweep {
     const unsigned long long *const s_tab;  // the c ln c table in shared memory
     const int table_smem;
     const unsigned long long *const g_tab;
+    // OVL: the first bin's and the previous bin's offsets, or with kPairWords
+    // their words ([s][0])
     unsigned int first[TPT][NF] = {}, prev[TPT][NF] = {};
 
     // T(c) for the byte offset o = 8 c
@@ -421,15 +441,29 @@ struct Sweep {
 #pragma unroll
             for (int g = 0; g < G; ++g) {
                 unsigned int o[NF];
-                v[s][g] = F::get(v[s][g], o);  // v now holds the word to store
-#pragma unroll
-                for (int f = 0; f < NF; ++f) {
-                    if (OVL) {
-                        if (PEEL && g == 0) first[s][f] = o[f];
-                        else add(t[s], f, look(prev[s][f] + o[f]));
-                        prev[s][f] = o[f];
+                if constexpr (OVL && F::kPairWords) {
+                    // the overlapping bin's counts from the sum of its fine words
+                    const unsigned int w0 = v[s][g];
+                    if (PEEL && g == 0) {
+                        first[s][0] = w0;
                     } else {
-                        add(t[s], f, look(o[f]));
+                        F::offsets(prev[s][0] + w0, o);
+#pragma unroll
+                        for (int f = 0; f < NF; ++f) add(t[s], f, look(o[f]));
+                    }
+                    prev[s][0] = w0;
+                    v[s][g] = F::next(w0);
+                } else {
+                    v[s][g] = F::get(v[s][g], o);  // v now holds the word to store
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) {
+                        if (OVL) {
+                            if (PEEL && g == 0) first[s][f] = o[f];
+                            else add(t[s], f, look(prev[s][f] + o[f]));
+                            prev[s][f] = o[f];
+                        } else {
+                            add(t[s], f, look(o[f]));
+                        }
                     }
                 }
             }
@@ -475,7 +509,15 @@ struct Sweep {
             j += 2;
         }
         if (j < n) step<1, false>(w, acc);
-        if (OVL) {
+        if constexpr (OVL && F::kPairWords) {
+#pragma unroll
+            for (int s = 0; s < TPT; ++s) {
+                unsigned int o[NF];
+                F::offsets(prev[s][0] + first[s][0], o);
+#pragma unroll
+                for (int f = 0; f < NF; ++f) add(acc[s], f, look(o[f]));
+            }
+        } else if (OVL) {
 #pragma unroll
             for (int s = 0; s < TPT; ++s)
 #pragma unroll
@@ -775,7 +817,7 @@ __global__ void __launch_bounds__(1 << LOG2B, main_min_blocks(TPT, LOG2B, KV)) k
                 const int s0 = s_seg[i], s1 = s_seg[i + 1];
                 const int ka = max(s0, lo), kb = min(s1, hi);
                 if (ka < kb) {
-                    const unsigned int inc = (pk2 && (ended & 1)) ? kPk2IncB : 1u;
+                    const unsigned int inc = pk2 ? ((ended & 1) ? kPk2IncB : 1u) + kPk2IncC : 1u;
                     compiler_fence();
                     const void *pp = s_pts;
                     constexpr bool HP = MODE != GCE_PHASE_FP64;  // half points exist
