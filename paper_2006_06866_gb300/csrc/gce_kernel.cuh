@@ -496,14 +496,19 @@ struct Sweep {
         int w[TPT];
 #pragma unroll
         for (int s = 0; s < TPT; ++s) w[s] = w0[s];
-        // bins per step: about four words in flight
-        constexpr int G = TPT * NF >= 4 ? 2 : 4;
+        // bins per step: four to eight words in flight, eight bins with one trial
+        // per thread (+1 % over four at 50 overlapping bins)
+        constexpr int G = TPT * NF >= 4 ? 2 : (TPT == 1 ? 8 : 4);
         int j = 0;
         if (OVL) {
             step<1, true>(w, acc);
             j = 1;
         }
         for (; j + G <= n; j += G) step<G, false>(w, acc);
+        if (G > 4 && (n - j) >= 4) {
+            step<4, false>(w, acc);
+            j += 4;
+        }
         if (G > 2 && (n - j) >= 2) {
             step<2, false>(w, acc);
             j += 2;

@@ -68,6 +68,36 @@ def test_overlapping_bins_grid(h, mode, n_phase):
         assert np.array_equal(single, got.astype(np.float32))
 
 
+@pytest.mark.parametrize("mode", MODES)
+def test_overlap_packed_counter_limits(h, mode):
+    """Overlapping bins on curves of 1023 points (the largest with two segments and the
+    cumulative count packed in one counter word) and 1024 (the snapshot format): at the
+    trial period P0 every point folds into one fine bin, half of them in the first
+    magnitude segment and half in the last, so both segment fields, the cumulative field
+    and the sums of two fine words reach their largest values (and H = ln 2 there).  Every cell against the
+    oracle, with trials on both sides of P0."""
+    p0, n_phase = 1.7, 50
+    ts, ms, lengths = [], [], (1023, 1024)
+    for n in lengths:
+        k = np.arange(n, dtype=np.float64)
+        ts.append(p0 * (k + 0.3 / n_phase))  # phase 0.006 at P0: inside fine bin 0
+        ms.append(np.where(k < n // 2, 15.0, 16.0))
+    offs = np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64)
+    periods = p0 * (1.0 + 2e-5 * np.linspace(-1.0, 1.0, 33))
+    assert periods[16] == p0
+    b = synth.LightCurveBatch("limits", np.concatenate(ts), np.concatenate(ms), offs, periods,
+                              np.zeros(1), n_phase, 10, np.zeros(2), np.zeros(2), np.zeros(2))
+    cfg = g.Config(n_phase, 10, mode, overlap=True)
+    got = g.gce_ce_grid(h, cfg=cfg, **dev_args(b))
+    assert g.gce_stream_status(h) == g.GCE_OK
+    got = got.cpu().numpy().astype(np.float64)
+    ref, dmin = oracle.Oracle().ce_grid(b.times, b.mags, b.offsets, b.periods, b.pdots, n_phase,
+                                        10, with_dmin=True, overlap=True)
+    # at P0 each overlapping bin holds the two segments half and half: H = ln 2
+    assert abs(ref[1, 0, 16] - np.log(2.0)) < 1e-12
+    compare_grid(mode, got, ref, dmin)
+
+
 def test_overlap_needs_two_bins(h):
     b = batch()
     with pytest.raises(g.GceError):
