@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gce", choices=["gce", "reference"])
     ap.add_argument("--mode", default="split32", choices=["split32", "fixed32", "fp64"])
-    ap.add_argument("--workload", type=int, default=1, help="synthetic workload index (0..4)")
+    ap.add_argument("--workload", type=int, default=1, help="synthetic workload index (0..5)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64 / SPLIT32 / one-launch-per-curve comparison legs")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
