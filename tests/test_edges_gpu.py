@@ -139,6 +139,7 @@ def test_autotune_on_the_job(h, pdots):
     g.gce_autotune_job(h, cfg=cfg, **args)
     t = g.gce_get_tuning(h, cfg, 400, n_pdots=len(pdots))
     assert t["block"] in (128, 256, 512) and t["tpt"] in (1, 2, 4)
+    assert t["slot_range"] in (0, 1)  # the tuner may keep the mid SPLIT32 slot range
     after = g.gce_ce_grid(h, cfg=cfg, **args).cpu().numpy()
     assert np.array_equal(before, after)
 
@@ -146,6 +147,8 @@ def test_autotune_on_the_job(h, pdots):
 def test_four_trials_per_thread_not_built_for_fp64(h):
     with pytest.raises(g.GceError):
         g.gce_set_tuning(h, g.Config(15, 10, "fp64"), 500, block=128, tpt=4)
+    with pytest.raises(g.GceError):  # slot ranges: 0 (wide) and 1 (mid) only
+        g.gce_set_tuning(h, g.Config(15, 10, "split32"), 500, block=128, tpt=2, slot_range=2)
     g.gce_set_tuning(h, g.Config(15, 10, "split32"), 500, block=128, tpt=4)
 
 
